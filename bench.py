@@ -1,0 +1,383 @@
+"""Throughput of one multi-view training step of EWA splatting on GB300.
+
+A step is one pass of the whole hot path over one batch of V views of a
+resident scene: participation + projection + colour, (view, tile, depth)
+binning and sort, front-to-back blending, 0.8 L1 + 0.2 D-SSIM loss and its
+gradient, back-to-front blend backward, reduction of the gradients across
+views onto the 3D Gaussians, and the multi-view densification statistics.
+
+Prints one JSON line.  `value` is views per second of the batched path
+(inputs resident in HBM), `e2e` the same through the C ABI with the scene and
+the targets copied from pinned host memory and the loss copied back every
+step.  `--impl reference` times the CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "multiview_500k_4x1264x832"
+LAMBDA = 0.2
+METRIC = "fwd+bwd views/s (batched multi-view vs per-view loop) at oracle tol; serve p50/p99"
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--no-loop", action="store_true", help="skip the per-view launch loop")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+    from paper_2506_12727_gb300 import build as lib_build
+    lib_build.build()
+    from paper_2506_12727_gb300 import mvgs
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    tile = tuple(int(x) for x in args.tile.split("x"))
+    scene, cams, extra = synth.workload(args.workload)
+    V, n = cams.V, scene.n
+    targets = synth.make_targets(cams)
+    hw = np.stack([cams.height, cams.width], 1).astype(np.int32)
+    dev = "cuda"
+    params = {k: torch.tensor(getattr(scene, k), device=dev).contiguous() for k in
+              ("means", "log_scales", "quats", "opacity_logits", "sh")}
+    tgt = torch.tensor(synth.pack_images(targets), device=dev)
+    sc = mvgs.make_scene(params, scene.sh_degree)
+    rz = mvgs.Rasterizer(cams, tile=tile)
+    grads = {k: torch.empty_like(v) for k, v in params.items()}
+    dssim_ws = torch.empty(mvgs.dssim_workspace_size(hw), dtype=torch.uint8, device=dev)
+    loss = torch.empty(V, device=dev)
+    dimg = torch.empty_like(tgt)
+    acc = [torch.zeros(n, device=dev) for _ in range(3)]
+    gm2d = None
+    e1 = None
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+
+    def step(rast, scene_c, target, hw_, loss_, dimg_, ws_):
+        nonlocal gm2d, e1
+        img = rast.forward(scene_c)
+        mvgs.dssim_loss(img, target, hw_, LAMBDA, loss_, dimg_, ws_)
+        R = int(rast.needed.records)
+        if gm2d is None or gm2d.shape[0] < R:
+            gm2d = torch.empty(int(R * 1.2) + 16, 2, device=dev)
+            e1 = torch.empty(int(R * 1.2) + 16, device=dev)
+        rast.backward(scene_c, dimg_, grads, gm2d, e1)
+        mvgs.adc_accumulate(rast.state, n, gm2d, e1, *acc)
+
+    def timed(fn, steps, warmup, profile=False):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        if profile:
+            mvgs.profile_read()
+            mvgs.profile_enable(True)
+        ms = []
+        s = torch.cuda.current_stream()
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            b.record(s)
+            ms.append((a, b))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        stages = None
+        if profile:
+            mvgs.profile_enable(False)
+            stages = mvgs.profile_read()
+        total = sum(a.elapsed_time(b) for a, b in ms)
+        return total / steps, stages
+
+    # ---- batched multi-view step (the headline) ----
+    clocks = ClockSampler(local)
+    launches0 = mvgs.launch_count()
+    clocks.start()
+    ms_batched, stages = timed(lambda: step(rz, sc, tgt, hw, loss, dimg, dssim_ws), args.steps, args.warmup,
+                               profile=True)
+    clk = clocks.stop()
+    launches = (mvgs.launch_count() - launches0)
+    launches_per_step = launches / float(args.steps + args.warmup)
+    if dist:
+        t = torch.tensor([ms_batched], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_batched = float(t.item())
+    needed = (int(rz.needed.records), int(rz.needed.keys))
+
+    # ---- per-view launch loop: the same library, V = 1, V times ----
+    loop = None
+    if not args.no_loop:
+        singles = []
+        for v in range(V):
+            cv = cams.subset([v])
+            hv = hw[v:v + 1]
+            off = synth.view_offsets(cams)
+            singles.append((mvgs.Rasterizer(cv, tile=tile), tgt[off[v]:off[v + 1]].contiguous(), hv,
+                            torch.empty(1, device=dev), torch.empty(int(off[v + 1] - off[v]), device=dev),
+                            torch.empty(mvgs.dssim_workspace_size(hv), dtype=torch.uint8, device=dev)))
+
+        def loop_step():
+            for rv, tv, hv, lv, dv, wv in singles:
+                step(rv, sc, tv, hv, lv, dv, wv)
+        ms_loop, _ = timed(loop_step, max(3, args.steps // 2), 2)
+        loop = {"views_per_s": V / (ms_loop / 1e3), "ms_per_step": ms_loop,
+                "speedup_batched_over_loop": ms_loop / ms_batched}
+
+    # ---- end to end through the C ABI with host buffers ----
+    host = {k: v.cpu().pin_memory() for k, v in params.items()}
+    host_tgt = tgt.cpu().pin_memory()
+    host_loss = torch.empty(V, pin_memory=True)
+    h2d = sum(t.numel() * 4 for t in host.values()) + host_tgt.numel() * 4
+    d2h = host_loss.numel() * 4
+
+    def e2e_step():
+        for k in params:
+            params[k].copy_(host[k], non_blocking=True)
+        tgt.copy_(host_tgt, non_blocking=True)
+        step(rz, sc, tgt, hw, loss, dimg, dssim_ws)
+        host_loss.copy_(loss, non_blocking=True)
+    ms_e2e, _ = timed(e2e_step, max(3, args.steps // 2), 2)
+
+    # ---- roofline of the dominant kernel ----
+    roof = roofline(stages, args, needed, rz, clk)
+
+    out = {
+        "metric": METRIC, "value": V * world / (ms_batched / 1e3), "unit": "views/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batched, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "gaussians": n, "sh_degree": scene.sh_degree, "views": V,
+                   "resolutions": sorted({f"{w}x{h}" for w, h in zip(cams.width, cams.height)}),
+                   "loss": "0.8 L1 + 0.2 D-SSIM (11x11, sigma 1.5)", "adc": True, "tile": args.tile,
+                   "records": needed[0], "keys": needed[1],
+                   "l2": "512 MB buffer written between timed steps (L2 is 129 MB); per-step working set > 1 GB",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": V * world / (ms_e2e / 1e3), "unit": "views/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "per_view_loop": loop,
+        "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in (stages or {}).items() if v[1]},
+        "roofline": roof,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(args.workload)
+    if dist:
+        dist.destroy_process_group()
+    return out
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def roofline(stages, args, needed, rz, clk):
+    """Achieved / peak for the stage with the largest time per step."""
+    if not stages:
+        return None
+    peaks, src = _peaks()
+    steps = args.steps
+    per_step = {k: v[0] / steps for k, v in stages.items() if v[1]}
+    dom = max(per_step, key=per_step.get)
+    ms_launch = stages[dom][0] / stages[dom][1]
+    R, K = needed
+    tiles = int(rz.layout.tiles)
+    bits = max(1, int(np.ceil(np.log2(max(tiles, 2)))))
+    passes = (bits + 7) // 8
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    if dom == "tile_sort":
+        traffic = passes * 16.0 * K  # read (key, value), write (key, value) per pass
+        ach = traffic / (ms_launch / 1e3) / 1e9
+        return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "peak_source": src,
+                "algorithmic": f"{passes} passes x 16 B x {K} keys"}
+    if dom in ("blend_forward", "blend_backward"):
+        rec = rz.records()
+        nc = rec["n_contrib"].to(torch.int64).sum().item()
+        flop_per_pair = 18.0 if dom == "blend_forward" else 60.0
+        flops = flop_per_pair * nc
+        mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1455.0)
+        peak = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        ach = flops / (ms_launch / 1e3) / 1e12
+        return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)",
+                "algorithmic": f"{flop_per_pair:.0f} FLOP x {nc} (pixel, list entry) pairs up to the last contributor"}
+    # other stages: bytes moved estimate
+    byte_est = {"preprocess": 236.0 * rz.n + 64.0 * R, "duplicate": 8.0 * K + 12.0 * R,
+                "depth_sort": 4 * 16.0 * R, "preprocess_backward": 236.0 * 2 * rz.n + 48.0 * R}
+    b = byte_est.get(dom)
+    if b is None:
+        return {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None}
+    ach = b / (ms_launch / 1e3) / 1e9
+    return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": None, "peak_source": src}
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle
+# ---------------------------------------------------------------------------
+def oracle_sample(workload, view=0, window=None):
+    """One bounded sample of the workload on the oracle: forward + loss +
+    backward of one view (optionally a pixel window of it).  Returns
+    (seconds, fraction of a full view the sample covers)."""
+    import oracle
+    scene, cams, extra = synth.workload(workload)
+    c1 = cams.subset([view])
+    targets = synth.make_targets(cams)
+    t0 = time.perf_counter()
+    fw = oracle.forward(scene, c1, (16, 16), window=window)
+    H, W = int(c1.height[0]), int(c1.width[0])
+    img = fw["img"].reshape(3, H, W)
+    tg = targets[view]
+    if window is not None:
+        x0, y0, x1, y1 = window[0]
+        img, tg = img[:, y0:y1, x0:x1], tg[:, y0:y1, x0:x1]
+    _, _, g = oracle.dssim_l1_loss([img], [tg], LAMBDA)
+    d = np.zeros((3, H, W))
+    if window is not None:
+        d[:, y0:y1, x0:x1] = g[0]
+    else:
+        d = g[0]
+    oracle.backward(scene, c1, fw, d.reshape(-1), (16, 16), window=window)
+    dt = time.perf_counter() - t0
+    frac = 1.0 if window is None else ((x1 - x0) * (y1 - y0)) / float(H * W)
+    return dt, frac
+
+
+def cpu_baseline(workload):
+    dt, frac = oracle_sample(workload)
+    return {"value": frac / dt, "unit": "views/s", "cores": 1, "kind": "oracle",
+            "sample": f"view 0 of {workload}, full resolution, forward + loss + backward, one thread",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    scene, cams, extra = synth.workload(args.workload)
+    W, H = int(cams.width[0]), int(cams.height[0])
+    win = np.array([[W // 2 - 128, H // 2 - 128, W // 2 + 128, H // 2 + 128]])
+    for _ in range(args.warmup):
+        oracle_sample(args.workload, window=win)
+    times = []
+    frac = None
+    for _ in range(args.steps):
+        dt, frac = oracle_sample(args.workload, window=win)
+        times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = frac / (ms / 1e3)
+    sample = f"256x256 window at the centre of view 0 of {args.workload}, forward + loss + backward, one thread"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "gaussians": scene.n, "views": cams.V, "tile": "16x16"},
+            "cpu_baseline": {"value": value, "unit": "views/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "views/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
+    out = run_reference(args, rank, world) if args.impl == "reference" else run_ours(args, rank, world)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * mvgs.h -- C ABI of the multi-view differentiable Gaussian-splatting
+ * rasterizer (sm_103a).
+ *
+ * The operations follow Choi, Kim & Kim, "Efficient multi-view training for
+ * 3D Gaussian Splatting" (ICCV 2025):
+ *   - mvgs_render_views          Eq. 1 rendered for a batch of V cameras with
+ *                                the preprocessing of the supplement
+ *                                ("Rasterization in multi-view training"):
+ *                                participation test, projection, duplication
+ *                                per tile, sort by (view, tile, depth), one
+ *                                block per (tile, view).
+ *   - mvgs_render_views_backward reverse-mode derivative of the above; a
+ *                                Gaussian seen in several views sums the
+ *                                gradients of all of them (Sec. 5.2).
+ *   - mvgs_dssim_loss            photometric l1 + D-SSIM (Sec. 3 and the SSIM
+ *                                equations of Sec. 5.1.2), per view.
+ *   - mvgs_adc_accumulate        the multi-view densification error metrics
+ *                                E_1 and E_2 of Sec. 5.2.2 (norm per pixel /
+ *                                per view, then add).
+ *
+ * Conventions shared by every call
+ *   - Pointers named d_* (and all image / parameter / gradient pointers) are
+ *     DEVICE pointers owned by the caller.  Camera arrays are HOST arrays.
+ *   - The library never allocates device memory.  Calls that need scratch take
+ *     a caller-owned `workspace`; the forward writes everything the backward
+ *     needs into a caller-owned `state` buffer.  Sizes come from
+ *     mvgs_render_layout() / mvgs_dssim_workspace_size().
+ *   - Every call is asynchronous on the given CUDA stream, except that
+ *     mvgs_render_views synchronises the stream twice to read the number of
+ *     visible (Gaussian, view) records and of duplicated keys back to the
+ *     host (they size the sorts).
+ *   - Every call returns an mvgs_status; no exception crosses the ABI.
+ *     mvgs_last_error() returns a message for the calling thread.
+ *   - Float data is IEEE float32.  Images are packed per view: view v
+ *     occupies [3 * P_v, 3 * P_{v+1}) of the buffer, P_v = sum_{u<v} H_u W_u,
+ *     each view stored channel-major [3, H, W].
+ */
+#ifndef MVGS_H
+#define MVGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* mvgs_stream;  /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum mvgs_status {
+    MVGS_OK = 0,
+    MVGS_EINVAL = 1,      /* bad argument: null pointer, V < 1, empty image, bad tile */
+    MVGS_ENOSPACE = 2,    /* state or workspace too small, or a capacity exceeded;
+                             the needed counts are reported and nothing is rendered */
+    MVGS_EOVERFLOW = 3,   /* a count does not fit the index types (keys >= 2^32,
+                             records >= 2^31, global tiles >= 2^32) */
+    MVGS_ECUDA = 4,       /* a CUDA launch or copy failed */
+    MVGS_EDEVICE = 5      /* a device-side check failed (e.g. a bounded wait expired) */
+} mvgs_status;
+
+/* Pinhole camera with OpenCV axes (+x right, +y down, +z forward).
+ * viewmat = [R | t], row-major 3x4, maps world points X to camera points
+ * R X + t.  campos is the camera centre in world space (used for the
+ * view-dependent colour).  Points with camera depth <= near_z are culled.
+ * A pixel (x, y) samples the image plane at (x + 0.5, y + 0.5). */
+typedef struct mvgs_camera {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float viewmat[12];
+    float campos[3];
+    float near_z;
+} mvgs_camera;
+
+/* The 3D Gaussians of Sec. 3: mean mu, scale S = diag(exp(log_scales)),
+ * rotation R from the quaternion (w, x, y, z) (normalised inside), opacity
+ * o = sigmoid(opacity_logits), colour from real spherical harmonics of
+ * degree sh_degree <= 3 (coefficients [n, (d+1)^2, 3]).  Device pointers,
+ * float32, contiguous. */
+typedef struct mvgs_scene {
+    int64_t n;
+    int32_t sh_degree;
+    int32_t reserved;
+    const float* means;          /* [n, 3] */
+    const float* log_scales;     /* [n, 3] */
+    const float* quats;          /* [n, 4] */
+    const float* opacity_logits; /* [n]    */
+    const float* sh;             /* [n, (d+1)^2, 3] */
+} mvgs_scene;
+
+/* Render settings.  tile_w x tile_h pixels form one tile; one CUDA block
+ * renders one (tile, view).  Supported: tile_w, tile_h multiples of 8 with
+ * 64 <= tile_w * tile_h <= 512 (8x8, 16x16, 16x32, ...).  The rendered
+ * image does not depend on the tile size: a pixel blends a Gaussian only when
+ * it lies within the Gaussian's radius on both axes, and every tile that
+ * holds such a pixel lists the Gaussian. */
+typedef struct mvgs_config {
+    int32_t tile_w, tile_h;
+    float bg[3];      /* background colour added with the final transmittance */
+    uint32_t flags;   /* reserved, must be 0 */
+} mvgs_config;
+
+/* Capacities the caller sized `state` and `workspace` for:
+ * records = visible (Gaussian, view) pairs, keys = (record, tile) pairs. */
+typedef struct mvgs_capacity {
+    int64_t records;
+    int64_t keys;
+} mvgs_capacity;
+
+/* Byte offsets of the arrays inside `state` (all 256-byte aligned), so a
+ * caller may read the intermediate results, and the total sizes. */
+typedef struct mvgs_layout {
+    size_t state_bytes;
+    size_t workspace_bytes;          /* forward and backward scratch (max of both) */
+    size_t off_counts;               /* int64[4]: records, keys, tiles, pixels     */
+    size_t off_rec_offsets;          /* int64[n + 1]: records of Gaussian g are
+                                        [off[g], off[g+1]) (Gaussian-major)       */
+    size_t off_rec_gauss;            /* int32[records]: Gaussian index            */
+    size_t off_rec_view;             /* int32[records]: view index                */
+    size_t off_rec_xy;               /* float2[records]: projected mean (pixels)   */
+    size_t off_rec_conic_opacity;    /* float4[records]: conic A, B, C; opacity   */
+    size_t off_rec_rgb;              /* float4[records]: rgb; .w = radius in pixels */
+    size_t off_rec_clamp;            /* int32[records]: bit c set if channel c was
+                                        clamped at 0                              */
+    size_t off_rec_depth;            /* float[records]: camera depth              */
+    size_t off_rec_rect;             /* int16x4[records]: tile x0, y0, x1, y1 (excl.) */
+    size_t off_sorted_records;       /* uint32[keys]: record ids sorted by (view, tile, depth, Gaussian) */
+    size_t off_tile_ranges;          /* int64x2[tiles]: [start, end) into the sorted ids */
+    size_t off_final_T;              /* float[pixels]: transmittance after blending */
+    size_t off_n_contrib;            /* uint32[pixels]: list position one past the last contributor */
+    int64_t tiles;                   /* total tiles over all views                 */
+    int64_t pixels;                  /* total pixels over all views                */
+} mvgs_layout;
+
+/* Fills `out` for a scene of n Gaussians, V host cameras and the capacities.
+ * Pure host arithmetic.  Returns MVGS_EINVAL / MVGS_EOVERFLOW on bad input. */
+mvgs_status mvgs_render_layout(int64_t n, const mvgs_camera* cams, int32_t V, const mvgs_config* cfg,
+                               const mvgs_capacity* cap, mvgs_layout* out);
+
+/* Forward render of V views (Eq. 1; preprocessing of the supplement).
+ *   images     [3 * pixels] float32 out, packed per view (see top).
+ *   state      >= layout.state_bytes, written; keep it for the backward.
+ *   workspace  >= layout.workspace_bytes, scratch.
+ *   needed     out (host): the record and key counts this batch needs.
+ * If a count exceeds `cap`, returns MVGS_ENOSPACE after reporting `needed`;
+ * the caller re-sizes with mvgs_render_layout and calls again.
+ * Synchronises `stream` twice (record and key count read-back). */
+mvgs_status mvgs_render_views(const mvgs_scene* scene, const mvgs_camera* cams, int32_t V, const mvgs_config* cfg,
+                              const mvgs_capacity* cap, float* images, void* state, size_t state_bytes,
+                              void* workspace, size_t workspace_bytes, mvgs_capacity* needed, mvgs_stream stream);
+
+/* Backward of mvgs_render_views for the same scene, cameras, config and
+ * capacity, given dL/dimages (packed like the images).  Overwrites
+ *   g_means [n,3], g_log_scales [n,3], g_quats [n,4] (w.r.t. the raw
+ *   quaternion), g_opacity_logits [n], g_sh [n,(d+1)^2,3]
+ * with gradients summed over all views.  Optional per-record outputs (NULL
+ * to skip), indexed like the state's record arrays:
+ *   g_mean2d [records, 2]  dL/d projected mean, pixel units;
+ *   e1       [records]     sum over pixels of the norm of each pixel's
+ *                          contribution to dL/d projected mean.
+ * `state` is read-only. */
+mvgs_status mvgs_render_views_backward(const mvgs_scene* scene, const mvgs_camera* cams, int32_t V,
+                                       const mvgs_config* cfg, const mvgs_capacity* cap, const float* dL_dimages,
+                                       const void* state, size_t state_bytes, void* workspace,
+                                       size_t workspace_bytes, float* g_means, float* g_log_scales, float* g_quats,
+                                       float* g_opacity_logits, float* g_sh, float* g_mean2d, float* e1,
+                                       mvgs_stream stream);
+
+/* Scratch bytes mvgs_dssim_loss needs for these views (hw: host [V, 2] of
+ * (height, width)). */
+size_t mvgs_dssim_workspace_size(const int32_t* hw, int32_t V);
+
+/* Per-view loss L_v = (1 - lambda) mean|I - I*| + lambda (1 - SSIM(I, I*)),
+ * SSIM with an 11x11 Gaussian window (sigma 1.5, normalised to sum 1), zero
+ * padding, C1 = 0.01^2, C2 = 0.03^2, averaged over the 3 channels and all
+ * pixels of the view.
+ *   img, target  packed images (see top)   loss_per_view [V] float32 out
+ *   dL_dimg      packed, out: d(mean_v L_v)/d img; NULL to skip.
+ * Deterministic (no atomics). */
+mvgs_status mvgs_dssim_loss(const float* img, const float* target, const int32_t* hw, int32_t V, float lambda,
+                            float* loss_per_view, float* dL_dimg, void* workspace, size_t workspace_bytes,
+                            mvgs_stream stream);
+
+/* Adds this batch's densification statistics into running per-Gaussian sums
+ * (Sec. 5.2.2):
+ *   accum_e1[g] += sum_views e1[record]           (E_1: norm, then add)
+ *   accum_e2[g] += sum_views || g_mean2d[record] || (E_2: add per view, norm)
+ *   denom[g]    += number of views in which g is visible
+ * `state` is the forward's state for the batch (its record map is read);
+ * g_mean2d / e1 are the per-record outputs of the backward. */
+mvgs_status mvgs_adc_accumulate(const void* state, int64_t n, const float* g_mean2d, const float* e1,
+                                float* accum_e1, float* accum_e2, float* denom, mvgs_stream stream);
+
+/* Optional stage timing (instrumentation; the paper has no counterpart).
+ * While enabled, every call records a pair of CUDA events around each of its
+ * stages on the call's stream (events are host objects; no device memory is
+ * allocated).  mvgs_profile_read waits for the recorded events, adds their
+ * durations to per-stage totals, copies up to max_stages totals (ms) and
+ * launch counts into the host arrays, resets them, and returns the number of
+ * stages.  Process-wide; intended for one calling thread at a time. */
+typedef enum mvgs_stage {
+    MVGS_STAGE_COUNT_VISIBLE = 0, /* participation count per (Gaussian, view)  */
+    MVGS_STAGE_SCAN_RECORDS,      /* record offsets                            */
+    MVGS_STAGE_PREPROCESS,        /* projection, colour, radius, rect          */
+    MVGS_STAGE_DEPTH_SORT,        /* records by depth                          */
+    MVGS_STAGE_SCAN_TILES,        /* key offsets                               */
+    MVGS_STAGE_DUPLICATE,         /* one key per (record, tile)                */
+    MVGS_STAGE_TILE_SORT,         /* keys by (view, tile)                      */
+    MVGS_STAGE_RANGES,            /* per-tile list ranges                      */
+    MVGS_STAGE_BLEND_FORWARD,
+    MVGS_STAGE_ZERO_GRADS,
+    MVGS_STAGE_BLEND_BACKWARD,
+    MVGS_STAGE_PREPROCESS_BACKWARD,
+    MVGS_STAGE_DSSIM,
+    MVGS_STAGE_ADC,
+    MVGS_STAGE_COUNT
+} mvgs_stage;
+mvgs_status mvgs_profile_enable(int32_t on);
+int32_t mvgs_profile_read(float* total_ms, int64_t* launches, int32_t max_stages);
+const char* mvgs_stage_name(int32_t stage);
+
+/* Number of CUDA kernels the library has launched in this process (all
+ * threads and streams), for accounting in benchmarks. */
+int64_t mvgs_launch_count(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* mvgs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MVGS_H */

@@ -30,8 +30,8 @@ CAM_STRIDE = 22
 # record-level ambiguity bits (see mvgs_oracle.c)
 RA_RADIUS, RA_RGB_CLAMP, RA_J_CLAMP, RA_NEAR = 1, 2, 4, 8
 # pixel-level ambiguity bits
-PA_SUPPORT, PA_ALPHA_MIN, PA_T_MIN, PA_DEPTH_TIE, PA_ALPHA_MAX, PA_RADIUS = 1, 2, 4, 8, 16, 32
-PA_FORWARD = PA_SUPPORT | PA_ALPHA_MIN | PA_T_MIN | PA_DEPTH_TIE | PA_RADIUS
+PA_SUPPORT, PA_ALPHA_MIN, PA_T_MIN, PA_ALPHA_MAX, PA_RADIUS = 1, 2, 4, 16, 32
+PA_FORWARD = PA_SUPPORT | PA_ALPHA_MIN | PA_T_MIN | PA_RADIUS
 
 
 def build(force: bool = False) -> str:
@@ -108,24 +108,27 @@ def project(scene, cams, tile=(16, 16)) -> dict:
     return out
 
 
-def sort_keys(cams, tile, valid, rect, depth32):
+def sort_keys(cams, tile, valid, rect, depth32, window=None):
     """Keys (global tile << 32 | float32 depth bits) sorted by (key, Gaussian
     index); returns (keys uint64 [K], records int32 [K] = v*N+g, ranges int64
-    [tiles, 2])."""
+    [tiles, 2]).  With `window` ([V, 4] pixel boxes) only the tiles that
+    intersect the boxes get keys."""
     lib = _load()
     valid = _c(valid, np.int32)
     rect = _c(rect, np.int32)
     depth32 = _c(depth32, np.float32)
     V = cams.V
     N = valid.shape[0] // V
-    K = int(lib.orc_count_keys(ctypes.c_int(N), ctypes.c_int(V), _p(valid), _p(rect)))
+    win = _window_arg(cams, window)
+    K = int(lib.orc_count_keys(ctypes.c_int(N), ctypes.c_int(V), ctypes.c_int(tile[0]), ctypes.c_int(tile[1]),
+                               _p(valid), _p(rect), _p(win)))
     _, _, tile_base, _ = layout(cams, tile)
     keys = np.zeros(max(K, 1), np.uint64)
     recs = np.zeros(max(K, 1), np.int32)
     ranges = np.zeros((int(tile_base[-1]), 2), np.int64)
     ca = cams_array(cams)
     lib.orc_sort(ctypes.c_int(N), ctypes.c_int(V), _p(ca), ctypes.c_int(tile[0]), ctypes.c_int(tile[1]),
-                 _p(valid), _p(rect), _p(depth32), ctypes.c_int64(K), _p(keys), _p(recs), _p(ranges))
+                 _p(valid), _p(rect), _p(depth32), _p(win), ctypes.c_int64(K), _p(keys), _p(recs), _p(ranges))
     return keys[:K], recs[:K], ranges
 
 
@@ -242,7 +245,7 @@ def forward(scene, cams, tile=(16, 16), bg=(0.0, 0.0, 0.0), window=None):
     """Projection, sort and blend of all views; returns a dict with the
     projected records `P`, the sorted lists `S` and the render outputs."""
     P = project(scene, cams, tile)
-    S = sort_keys(cams, tile, P["valid"], P["rect"], P["depth"].astype(np.float32))
+    S = sort_keys(cams, tile, P["valid"], P["rect"], P["depth"].astype(np.float32), window)
     img, T, last, amb, chash = render(cams, P, S, bg, window, want_hash=True)
     return dict(P=P, S=S, img=img, T=T, last=last, amb=amb, chash=chash)
 

@@ -32,6 +32,11 @@
  * that threshold.  A float32 implementation may legitimately take the other
  * branch there, so tests compare such outputs loosely or not at all.
  *
+ * Depth order is not such a decision: the sort key holds the float32 depth,
+ * defined as the correctly rounded float32 of the camera-space depth, and an
+ * implementation must produce exactly those bits; equal keys are ordered by
+ * Gaussian index.
+ *
  * Every array is dense over (view, Gaussian): record r = v * N + g.
  */
 #include <math.h>
@@ -48,18 +53,21 @@ static const double K_GUARD = 1.3;
 static const double K_SIGMAS = 3.0;
 static const double K_EIG_FLOOR = 0.1;
 
-/* ---- ambiguity margins ------------------------------------------------- */
-static const double M_SUPPORT_PX = 2e-3;  /* |dx| vs r, pixels            */
-static const double M_ALPHA_REL = 1e-3;   /* alpha vs 1/255 and vs 0.99    */
-static const double M_T_REL = 5e-3;       /* T(1-alpha) vs 1e-4            */
-static const double M_RADIUS_REL = 1e-4;  /* 3 sqrt(lambda) vs an integer  */
-static const double M_DEPTH_REL = 4e-6;   /* two depths in one pixel list  */
-static const double M_CLAMP_ABS = 1e-5;   /* rgb vs 0, guard band          */
+/* ---- ambiguity margins ------------------------------------------------- *
+ * A decision is ambiguous when the compared quantity lies within the margin
+ * of its threshold (a float32 evaluation may take the other branch) AND the
+ * other branch would move the pixel by a non-negligible amount (M_EFFECT). */
+static const double M_SUPPORT_PX = 2e-3;  /* |dx| vs r, pixels                  */
+static const double M_ALPHA_REL = 2e-4;   /* alpha vs 1/255 and vs 0.99          */
+static const double M_T_REL = 1e-3;       /* T(1-alpha) vs 1e-4                  */
+static const double M_RADIUS_REL = 1e-4;  /* 3 sqrt(lambda) vs an integer        */
+static const double M_CLAMP_ABS = 1e-5;   /* rgb vs 0, guard band                */
+static const double M_EFFECT = 5e-6;      /* weight T alpha the flip would move  */
 
 /* record-level ambiguity bits */
 enum { RA_RADIUS = 1, RA_RGB_CLAMP = 2, RA_J_CLAMP = 4, RA_NEAR = 8 };
 /* pixel-level ambiguity bits */
-enum { PA_SUPPORT = 1, PA_ALPHA_MIN = 2, PA_T_MIN = 4, PA_DEPTH_TIE = 8, PA_ALPHA_MAX = 16, PA_RADIUS = 32 };
+enum { PA_SUPPORT = 1, PA_ALPHA_MIN = 2, PA_T_MIN = 4, PA_ALPHA_MAX = 16, PA_RADIUS = 32 };
 
 /* Camera record, passed as CAM_STRIDE doubles per view:
  * [0] width [1] height [2] fx [3] fy [4] cx [5] cy [6..14] R (world->camera,
@@ -375,11 +383,25 @@ static uint32_t f32_bits(float f) {
     return u;
 }
 
-/* Number of (record, tile) keys. */
-int64_t orc_count_keys(int N, int V, const int32_t* valid, const int32_t* rect) {
+/* Number of (record, tile) keys; with a pixel window per view, only the
+ * tiles that intersect the window are counted. */
+int64_t orc_count_keys(int N, int V, int tw, int th, const int32_t* valid, const int32_t* rect,
+                       const int32_t* window) {
     int64_t K = 0;
-    for (size_t r = 0; r < (size_t)N * V; r++)
-        if (valid[r]) K += (int64_t)(rect[4 * r + 2] - rect[4 * r]) * (rect[4 * r + 3] - rect[4 * r + 1]);
+    for (int v = 0; v < V; v++)
+        for (int g = 0; g < N; g++) {
+            size_t r = (size_t)v * N + g;
+            if (!valid[r]) continue;
+            int x0 = rect[4 * r], y0 = rect[4 * r + 1], x1 = rect[4 * r + 2], y1 = rect[4 * r + 3];
+            if (window) {
+                int wx0 = window[4 * v] / tw, wx1 = (window[4 * v + 2] - 1) / tw + 1;
+                int wy0 = window[4 * v + 1] / th, wy1 = (window[4 * v + 3] - 1) / th + 1;
+                x0 = x0 > wx0 ? x0 : wx0; x1 = x1 < wx1 ? x1 : wx1;
+                y0 = y0 > wy0 ? y0 : wy0; y1 = y1 < wy1 ? y1 : wy1;
+                if (x1 <= x0 || y1 <= y0) continue;
+            }
+            K += (int64_t)(x1 - x0) * (y1 - y0);
+        }
     return K;
 }
 
@@ -388,9 +410,11 @@ int64_t orc_count_keys(int N, int V, const int32_t* valid, const int32_t* rect) 
  * so the bits order like the value); sorts by (key, Gaussian index) and
  * returns the sorted keys, sorted record ids (v*N+g) and per global tile the
  * range [start, end) into the sorted arrays.  `depth32` is the depth already
- * rounded to float32. */
+ * rounded to float32.  With a pixel window per view (x0, y0, x1, y1), only
+ * keys of tiles that intersect the window are built. */
 void orc_sort(int N, int V, const double* cams, int tw, int th, const int32_t* valid, const int32_t* rect,
-              const float* depth32, int64_t K, uint64_t* keys_out, int32_t* recs_out, int64_t* ranges) {
+              const float* depth32, const int32_t* window, int64_t K, uint64_t* keys_out, int32_t* recs_out,
+              int64_t* ranges) {
     int64_t* tile_base = (int64_t*)malloc(sizeof(int64_t) * (V + 1));
     int* tiles_x = (int*)malloc(sizeof(int) * V);
     tile_base[0] = 0;
@@ -407,6 +431,9 @@ void orc_sort(int N, int V, const double* cams, int tw, int th, const int32_t* v
             if (!valid[r]) continue;
             for (int ty = rect[4 * r + 1]; ty < rect[4 * r + 3]; ty++)
                 for (int tx = rect[4 * r]; tx < rect[4 * r + 2]; tx++) {
+                    if (window && (tx < window[4 * v] / tw || tx > (window[4 * v + 2] - 1) / tw ||
+                                   ty < window[4 * v + 1] / th || ty > (window[4 * v + 3] - 1) / th))
+                        continue;
                     uint64_t gt = (uint64_t)(tile_base[v] + (int64_t)ty * tiles_x[v] + tx);
                     E[k].key = (gt << 32) | f32_bits(depth32[r]);
                     E[k].g = g;
@@ -456,7 +483,6 @@ static int blend_pixel(double px, double py, const int32_t* list, int64_t len, c
     *last = 0;
     *amb = 0;
     int n = 0;
-    double prev_depth = -1.0;
     for (int64_t i = 0; i < len; i++) {
         int32_t r = list[i];
         double mx = R->xy[2 * r], my = R->xy[2 * r + 1];
@@ -470,21 +496,19 @@ static int blend_pixel(double px, double py, const int32_t* list, int64_t len, c
         double ex = fabs(dx) > fabs(dy) ? fabs(dx) : fabs(dy); /* Chebyshev distance to the mean */
         /* support rule; a record whose radius is ambiguous may cover one more pixel ring */
         int inside = fabs(dx) <= rad && fabs(dy) <= rad;
-        if (alpha >= K_ALPHA_MIN * (1.0 - M_ALPHA_REL)) {
+        if (alpha >= K_ALPHA_MIN * (1.0 - M_ALPHA_REL) && T * alpha >= M_EFFECT) {
             if (fabs(ex - rad) < M_SUPPORT_PX) *amb |= PA_SUPPORT;
             if ((R->amb[r] & RA_RADIUS) && ex > rad - 1.0 - M_SUPPORT_PX && ex <= rad + 1.0 + M_SUPPORT_PX)
                 *amb |= PA_RADIUS;
         }
         if (!inside) continue;
         if (power > 0.0) continue;
-        if (fabs(alpha - K_ALPHA_MIN) < M_ALPHA_REL * K_ALPHA_MIN) *amb |= PA_ALPHA_MIN;
+        if (fabs(alpha - K_ALPHA_MIN) < M_ALPHA_REL * K_ALPHA_MIN && T * K_ALPHA_MIN >= M_EFFECT)
+            *amb |= PA_ALPHA_MIN;
         if (alpha < K_ALPHA_MIN) continue;
         if (fabs(ag - K_ALPHA_MAX) < M_ALPHA_REL * K_ALPHA_MAX) *amb |= PA_ALPHA_MAX;
-        double d = R->depth[r];
-        if (prev_depth > 0.0 && fabs(d - prev_depth) < M_DEPTH_REL * d) *amb |= PA_DEPTH_TIE;
-        prev_depth = d;
         double Tn = T * (1.0 - alpha);
-        if (fabs(Tn - K_T_MIN) < M_T_REL * K_T_MIN) *amb |= PA_T_MIN;
+        if (fabs(Tn - K_T_MIN) < M_T_REL * K_T_MIN && T * alpha >= M_EFFECT) *amb |= PA_T_MIN;
         if (Tn < K_T_MIN) break;
         for (int ch = 0; ch < 3; ch++) C[ch] += R->rgb[3 * r + ch] * alpha * T;
         if (out && n < cap) {

@@ -1,0 +1,545 @@
+// C ABI of libmvgs (declared in include/mvgs.h): argument checks, buffer
+// layout, and the launch sequence of each call.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/mvgs.h"
+#include "kernels.h"
+
+using namespace mvgs;
+
+namespace mvgs {
+static std::atomic<long long> g_launches{0};
+void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace mvgs
+
+namespace {
+
+thread_local std::string g_last_error;
+
+mvgs_status fail(mvgs_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+mvgs_status fail(mvgs_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+mvgs_status cuda_check(const char* where) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(MVGS_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+    return MVGS_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// ---- optional stage timing -------------------------------------------------
+struct Pending {
+    int stage;
+    cudaEvent_t a, b;
+};
+struct Profiler {
+    std::mutex mu;
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<Pending> pending;
+    double total[MVGS_STAGE_COUNT] = {};
+    long long calls[MVGS_STAGE_COUNT] = {};
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+Profiler& profiler() {
+    static Profiler p;
+    return p;
+}
+
+// Records events around one stage when timing is enabled.
+class StageTimer {
+  public:
+    StageTimer(int stage, cudaStream_t s) : stage_(stage), s_(s) {
+        Profiler& p = profiler();
+        std::lock_guard<std::mutex> lk(p.mu);
+        if (!p.on) return;
+        a_ = p.get();
+        b_ = p.get();
+        cudaEventRecord(a_, s_);
+    }
+    ~StageTimer() {
+        if (!a_) return;
+        Profiler& p = profiler();
+        std::lock_guard<std::mutex> lk(p.mu);
+        cudaEventRecord(b_, s_);
+        p.pending.push_back({stage_, a_, b_});
+    }
+
+  private:
+    int stage_;
+    cudaStream_t s_;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
+const char* kStageNames[MVGS_STAGE_COUNT] = {"count_visible", "scan_records", "preprocess", "depth_sort",
+                                             "scan_tiles", "duplicate", "tile_sort", "ranges", "blend_forward",
+                                             "zero_grads", "blend_backward", "preprocess_backward", "dssim", "adc"};
+
+// Sub-allocation of one caller buffer.
+struct Carver {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    }
+};
+
+struct Plan {
+    int V = 0;
+    long long n = 0;
+    std::vector<DevCam> cams;
+    long long tiles = 0, pixels = 0;
+    mvgs_layout L{};
+    // workspace offsets (forward)
+    size_t w_cams = 0, w_counts = 0, w_vis = 0, w_scan = 0, w_dkeys_a = 0, w_dkeys_b = 0, w_ids_a = 0, w_ids_b = 0,
+           w_order = 0, w_tiles = 0, w_tile_off = 0, w_keys_a = 0, w_keys_b = 0, w_vals_a = 0, w_vals_b = 0,
+           w_radix = 0;
+    // workspace offsets (backward)
+    size_t b_cams = 0, b_grad = 0;
+};
+
+mvgs_status check_config(const mvgs_config* cfg) {
+    if (!cfg) return fail(MVGS_EINVAL, "config is NULL");
+    const int tw = cfg->tile_w, th = cfg->tile_h;
+    if (tw < 8 || th < 8 || tw % 8 || th % 8 || tw * th > 512 || tw * th < 64)
+        return fail(MVGS_EINVAL, "unsupported tile %dx%d (multiples of 8, 64..512 pixels)", tw, th);
+    if (cfg->flags != 0) return fail(MVGS_EINVAL, "flags must be 0");
+    return MVGS_OK;
+}
+
+mvgs_status make_plan(long long n, const mvgs_camera* cams, int V, const mvgs_config* cfg, const mvgs_capacity* cap,
+                      Plan& P) {
+    if (n < 0) return fail(MVGS_EINVAL, "n < 0");
+    if (V < 1 || !cams) return fail(MVGS_EINVAL, "need at least one camera");
+    if (V > 65535) return fail(MVGS_EOVERFLOW, "at most 65535 views per call");
+    if (!cap || cap->records < 0 || cap->keys < 0) return fail(MVGS_EINVAL, "bad capacity");
+    mvgs_status st = check_config(cfg);
+    if (st != MVGS_OK) return st;
+    if (cap->records >= (1LL << 31)) return fail(MVGS_EOVERFLOW, "record capacity must be < 2^31");
+    if (cap->keys >= (1LL << 32)) return fail(MVGS_EOVERFLOW, "key capacity must be < 2^32");
+    const int tw = cfg->tile_w, th = cfg->tile_h;
+    P.V = V;
+    P.n = n;
+    P.cams.resize(V);
+    long long tiles = 0, pixels = 0;
+    for (int v = 0; v < V; v++) {
+        const mvgs_camera& c = cams[v];
+        if (c.width < 1 || c.height < 1) return fail(MVGS_EINVAL, "view %d: empty image", v);
+        if (!(c.fx > 0.f) || !(c.fy > 0.f)) return fail(MVGS_EINVAL, "view %d: focal lengths must be > 0", v);
+        const int txs = (c.width + tw - 1) / tw, tys = (c.height + th - 1) / th;
+        if (txs > 32767 || tys > 32767) return fail(MVGS_EOVERFLOW, "view %d: more than 32767 tiles per axis", v);
+        DevCam& d = P.cams[v];
+        for (int i = 0; i < 3; i++) {
+            for (int j = 0; j < 3; j++) d.R[3 * i + j] = c.viewmat[4 * i + j];
+            d.t[i] = c.viewmat[4 * i + 3];
+            d.campos[i] = c.campos[i];
+        }
+        d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+        d.near_z = c.near_z;
+        d.limx = kGuard * 0.5f * (float)c.width / c.fx;
+        d.limy = kGuard * 0.5f * (float)c.height / c.fy;
+        d.W = c.width; d.H = c.height;
+        d.tiles_x = txs; d.tiles_y = tys;
+        d.tile_base = tiles;
+        d.pix_base = pixels;
+        tiles += (long long)txs * tys;
+        pixels += (long long)c.width * c.height;
+    }
+    if (tiles >= (1LL << 32)) return fail(MVGS_EOVERFLOW, "more than 2^32 tiles over all views");
+    P.tiles = tiles;
+    P.pixels = pixels;
+
+    const size_t R = (size_t)cap->records, K = (size_t)cap->keys;
+    mvgs_layout& L = P.L;
+    std::memset(&L, 0, sizeof(L));
+    Carver s;
+    L.off_counts = s.take(4 * sizeof(long long));
+    L.off_rec_offsets = s.take((size_t)(n + 1) * sizeof(long long));
+    L.off_rec_gauss = s.take(R * sizeof(int));
+    L.off_rec_view = s.take(R * sizeof(int));
+    L.off_rec_xy = s.take(R * sizeof(float2));
+    L.off_rec_conic_opacity = s.take(R * sizeof(float4));
+    L.off_rec_rgb = s.take(R * sizeof(float4));
+    L.off_rec_clamp = s.take(R * sizeof(int));
+    L.off_rec_depth = s.take(R * sizeof(float));
+    L.off_rec_rect = s.take(R * sizeof(short4));
+    L.off_sorted_records = s.take(K * sizeof(uint32_t));
+    L.off_tile_ranges = s.take((size_t)tiles * 2 * sizeof(long long));
+    L.off_final_T = s.take((size_t)pixels * sizeof(float));
+    L.off_n_contrib = s.take((size_t)pixels * sizeof(uint32_t));
+    L.state_bytes = s.off;
+    L.tiles = tiles;
+    L.pixels = pixels;
+
+    Carver w;
+    P.w_cams = w.take((size_t)V * sizeof(DevCam));
+    P.w_counts = w.take((size_t)(n > 0 ? n : 1) * sizeof(int));
+    P.w_vis = w.take((size_t)(n > 0 ? n : 1) * V);
+    const size_t big = R > K ? R : K;
+    P.w_scan = w.take(scan_temp_bytes(big > (size_t)n ? big : (size_t)n));
+    P.w_dkeys_a = w.take(R * sizeof(uint32_t));
+    P.w_dkeys_b = w.take(R * sizeof(uint32_t));
+    P.w_ids_a = w.take(R * sizeof(uint32_t));
+    P.w_ids_b = w.take(R * sizeof(uint32_t));
+    P.w_order = w.take(R * sizeof(uint32_t));
+    P.w_tiles = w.take(R * sizeof(uint32_t));
+    P.w_tile_off = w.take((R + 1) * sizeof(unsigned long long));
+    P.w_keys_a = w.take(K * sizeof(uint32_t));
+    P.w_keys_b = w.take(K * sizeof(uint32_t));
+    P.w_vals_a = w.take(K * sizeof(uint32_t));
+    P.w_vals_b = w.take(K * sizeof(uint32_t));
+    P.w_radix = w.take(radix_temp_bytes(big));
+    const size_t fwd_bytes = w.off;
+    Carver b;
+    P.b_cams = b.take((size_t)V * sizeof(DevCam));
+    P.b_grad = b.take(R * kGradStride * sizeof(float));
+    L.workspace_bytes = fwd_bytes > b.off ? fwd_bytes : b.off;
+    return MVGS_OK;
+}
+
+mvgs_status check_scene(const mvgs_scene* sc) {
+    if (!sc) return fail(MVGS_EINVAL, "scene is NULL");
+    if (sc->n < 0) return fail(MVGS_EINVAL, "scene n < 0");
+    if (sc->sh_degree < 0 || sc->sh_degree > 3) return fail(MVGS_EINVAL, "sh_degree must be 0..3");
+    if (sc->n > 0 && (!sc->means || !sc->log_scales || !sc->quats || !sc->opacity_logits || !sc->sh))
+        return fail(MVGS_EINVAL, "scene has a NULL parameter array");
+    if (sc->n >= (1LL << 31)) return fail(MVGS_EOVERFLOW, "at most 2^31 - 1 Gaussians");
+    return MVGS_OK;
+}
+
+template <class T>
+T* at(void* base, size_t off) {
+    return reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+template <class T>
+const T* at(const void* base, size_t off) {
+    return reinterpret_cast<const T*>(static_cast<const char*>(base) + off);
+}
+
+RecordArgs record_args(void* state, const mvgs_layout& L) {
+    RecordArgs r;
+    r.rec_off = at<long long>(state, L.off_rec_offsets);
+    r.rec_g = at<int>(state, L.off_rec_gauss);
+    r.rec_v = at<int>(state, L.off_rec_view);
+    r.xy = at<float2>(state, L.off_rec_xy);
+    r.conic_o = at<float4>(state, L.off_rec_conic_opacity);
+    r.rgb_r = at<float4>(state, L.off_rec_rgb);
+    r.clamp = at<int>(state, L.off_rec_clamp);
+    r.depth = at<float>(state, L.off_rec_depth);
+    r.rect = at<short4>(state, L.off_rec_rect);
+    return r;
+}
+
+SceneArgs scene_args(const mvgs_scene* sc) {
+    SceneArgs a;
+    a.n = sc->n;
+    a.sh_degree = sc->sh_degree;
+    a.means = sc->means;
+    a.log_scales = sc->log_scales;
+    a.quats = sc->quats;
+    a.logits = sc->opacity_logits;
+    a.sh = sc->sh;
+    return a;
+}
+
+__global__ void set_counts_kernel(long long* c, long long R, long long K, long long T, long long P) {
+    c[0] = R;
+    c[1] = K;
+    c[2] = T;
+    c[3] = P;
+}
+
+int bits_for(long long tiles) {
+    int b = 0;
+    while (b < 63 && (1LL << b) < tiles) b++;
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mvgs_last_error(void) { return g_last_error.c_str(); }
+
+mvgs_status mvgs_profile_enable(int32_t on) {
+    Profiler& p = profiler();
+    std::lock_guard<std::mutex> lk(p.mu);
+    p.on = on != 0;
+    return MVGS_OK;
+}
+
+int32_t mvgs_profile_read(float* total_ms, int64_t* launches, int32_t max_stages) {
+    Profiler& p = profiler();
+    std::lock_guard<std::mutex> lk(p.mu);
+    for (const Pending& e : p.pending) {
+        float ms = 0.f;
+        cudaEventSynchronize(e.b);
+        if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+            p.total[e.stage] += ms;
+            p.calls[e.stage] += 1;
+        }
+        p.pool.push_back(e.a);
+        p.pool.push_back(e.b);
+    }
+    p.pending.clear();
+    const int n = max_stages < MVGS_STAGE_COUNT ? max_stages : MVGS_STAGE_COUNT;
+    for (int i = 0; i < n; i++) {
+        if (total_ms) total_ms[i] = (float)p.total[i];
+        if (launches) launches[i] = p.calls[i];
+    }
+    for (int i = 0; i < MVGS_STAGE_COUNT; i++) {
+        p.total[i] = 0.0;
+        p.calls[i] = 0;
+    }
+    return MVGS_STAGE_COUNT;
+}
+
+int64_t mvgs_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char* mvgs_stage_name(int32_t stage) {
+    return stage >= 0 && stage < MVGS_STAGE_COUNT ? kStageNames[stage] : "";
+}
+
+mvgs_status mvgs_render_layout(int64_t n, const mvgs_camera* cams, int32_t V, const mvgs_config* cfg,
+                               const mvgs_capacity* cap, mvgs_layout* out) {
+    if (!out) return fail(MVGS_EINVAL, "layout output is NULL");
+    Plan P;
+    const mvgs_status st = make_plan(n, cams, V, cfg, cap, P);
+    if (st != MVGS_OK) return st;
+    *out = P.L;
+    return MVGS_OK;
+}
+
+mvgs_status mvgs_render_views(const mvgs_scene* scene, const mvgs_camera* cams, int32_t V, const mvgs_config* cfg,
+                              const mvgs_capacity* cap, float* images, void* state, size_t state_bytes,
+                              void* workspace, size_t workspace_bytes, mvgs_capacity* needed, mvgs_stream stream) {
+    mvgs_status st = check_scene(scene);
+    if (st != MVGS_OK) return st;
+    Plan P;
+    st = make_plan(scene->n, cams, V, cfg, cap, P);
+    if (st != MVGS_OK) return st;
+    const mvgs_layout& L = P.L;
+    if (!images || !state || !workspace) return fail(MVGS_EINVAL, "NULL images, state or workspace");
+    if (state_bytes < L.state_bytes || workspace_bytes < L.workspace_bytes)
+        return fail(MVGS_ENOSPACE, "state %zu < %zu or workspace %zu < %zu bytes", state_bytes, L.state_bytes,
+                    workspace_bytes, L.workspace_bytes);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const long long n = scene->n;
+    const int tw = cfg->tile_w, th = cfg->tile_h;
+    DevCam* dcams = at<DevCam>(workspace, P.w_cams);
+    upload_cams(P.cams.data(), V, dcams, s);
+    const SceneArgs sc = scene_args(scene);
+    RecordArgs rec = record_args(state, L);
+    long long* counts_dev = at<long long>(state, L.off_counts);
+
+    // participation: which (Gaussian, view) pairs are visible, Gaussian-major
+    int* counts = at<int>(workspace, P.w_counts);
+    {
+        StageTimer t(MVGS_STAGE_COUNT_VISIBLE, s);
+        launch_count_visible(sc, dcams, V, tw, th, counts, at<uint8_t>(workspace, P.w_vis), s);
+    }
+    {
+        StageTimer t(MVGS_STAGE_SCAN_RECORDS, s);
+        scan_i32_to_i64(counts, rec.rec_off, (uint64_t)n, at<void>(workspace, P.w_scan), s);
+    }
+    long long R = 0;
+    if (cudaMemcpyAsync(&R, rec.rec_off + n, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return cuda_check("record count read-back");
+    if ((st = cuda_check("participation")) != MVGS_OK) return st;
+    if (needed) {
+        needed->records = R;
+        needed->keys = 0;
+    }
+    if (R > cap->records)
+        return fail(MVGS_ENOSPACE, "%lld visible records exceed the capacity of %lld", R, (long long)cap->records);
+
+    // projection, colour, radius and tile rectangle of every record
+    uint32_t* dkeys_a = at<uint32_t>(workspace, P.w_dkeys_a);
+    uint32_t* ids_a = at<uint32_t>(workspace, P.w_ids_a);
+    uint32_t* tiles = at<uint32_t>(workspace, P.w_tiles);
+    {
+        StageTimer t(MVGS_STAGE_PREPROCESS, s);
+        launch_preprocess(sc, dcams, V, tw, th, at<uint8_t>(workspace, P.w_vis), rec, dkeys_a, ids_a, tiles, s);
+    }
+
+    // records by depth, then keys per covered tile in that order
+    uint32_t* order = at<uint32_t>(workspace, P.w_order);
+    uint32_t* dkeys_sorted = nullptr;
+    {
+        StageTimer t(MVGS_STAGE_DEPTH_SORT, s);
+        radix_sort_pairs(dkeys_a, ids_a, at<uint32_t>(workspace, P.w_dkeys_b), at<uint32_t>(workspace, P.w_ids_b),
+                         order, &dkeys_sorted, (uint64_t)R, 32, at<void>(workspace, P.w_radix), s);
+    }
+    unsigned long long* tile_off = at<unsigned long long>(workspace, P.w_tile_off);
+    {
+        StageTimer t(MVGS_STAGE_SCAN_TILES, s);
+        scan_gather_u32_to_u64(tiles, order, tile_off, (uint64_t)R, at<void>(workspace, P.w_scan), s);
+    }
+    unsigned long long K = 0;
+    if (cudaMemcpyAsync(&K, tile_off + R, sizeof(K), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return cuda_check("key count read-back");
+    if ((st = cuda_check("preprocess")) != MVGS_OK) return st;
+    if (needed) needed->keys = (long long)K;
+    if (K >= (1ULL << 32)) return fail(MVGS_EOVERFLOW, "%llu keys do not fit 32-bit positions", K);
+    if ((long long)K > cap->keys)
+        return fail(MVGS_ENOSPACE, "%llu keys exceed the capacity of %lld", K, (long long)cap->keys);
+
+    uint32_t* keys_a = at<uint32_t>(workspace, P.w_keys_a);
+    uint32_t* vals_a = at<uint32_t>(workspace, P.w_vals_a);
+    {
+        StageTimer t(MVGS_STAGE_DUPLICATE, s);
+        launch_duplicate(order, tile_off, (uint64_t)R, K, rec.rect, rec.rec_v, dcams, P.tiles, keys_a, vals_a, s);
+    }
+    uint32_t* sorted = at<uint32_t>(state, L.off_sorted_records);
+    uint32_t* keys_sorted = nullptr;
+    {
+        StageTimer t(MVGS_STAGE_TILE_SORT, s);
+        radix_sort_pairs(keys_a, vals_a, at<uint32_t>(workspace, P.w_keys_b), at<uint32_t>(workspace, P.w_vals_b),
+                         sorted, &keys_sorted, K, bits_for(P.tiles), at<void>(workspace, P.w_radix), s);
+    }
+    long long* ranges = at<long long>(state, L.off_tile_ranges);
+    {
+        StageTimer t(MVGS_STAGE_RANGES, s);
+        launch_tile_ranges(keys_sorted, K, ranges, P.tiles, s);
+    }
+    set_counts_kernel<<<1, 1, 0, s>>>(counts_dev, R, (long long)K, P.tiles, P.pixels);
+    note_launches(1);
+
+    BlendArgs ba;
+    ba.cams = dcams;
+    ba.V = V;
+    ba.tw = tw;
+    ba.th = th;
+    ba.tiles = P.tiles;
+    ba.ranges = ranges;
+    ba.sorted = sorted;
+    ba.xy = rec.xy;
+    ba.conic_o = rec.conic_o;
+    ba.rgb_r = rec.rgb_r;
+    for (int i = 0; i < 3; i++) ba.bg[i] = cfg->bg[i];
+    {
+        StageTimer t(MVGS_STAGE_BLEND_FORWARD, s);
+        launch_blend_forward(ba, images, at<float>(state, L.off_final_T), at<uint32_t>(state, L.off_n_contrib), s);
+    }
+    return cuda_check("render");
+}
+
+mvgs_status mvgs_render_views_backward(const mvgs_scene* scene, const mvgs_camera* cams, int32_t V,
+                                       const mvgs_config* cfg, const mvgs_capacity* cap, const float* dL_dimages,
+                                       const void* state, size_t state_bytes, void* workspace,
+                                       size_t workspace_bytes, float* g_means, float* g_log_scales, float* g_quats,
+                                       float* g_opacity_logits, float* g_sh, float* g_mean2d, float* e1,
+                                       mvgs_stream stream) {
+    mvgs_status st = check_scene(scene);
+    if (st != MVGS_OK) return st;
+    Plan P;
+    st = make_plan(scene->n, cams, V, cfg, cap, P);
+    if (st != MVGS_OK) return st;
+    const mvgs_layout& L = P.L;
+    if (!dL_dimages || !state || !workspace) return fail(MVGS_EINVAL, "NULL gradient, state or workspace");
+    if (scene->n > 0 && (!g_means || !g_log_scales || !g_quats || !g_opacity_logits || !g_sh))
+        return fail(MVGS_EINVAL, "NULL parameter gradient");
+    if (state_bytes < L.state_bytes || workspace_bytes < L.workspace_bytes)
+        return fail(MVGS_ENOSPACE, "state %zu < %zu or workspace %zu < %zu bytes", state_bytes, L.state_bytes,
+                    workspace_bytes, L.workspace_bytes);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DevCam* dcams = at<DevCam>(workspace, P.b_cams);
+    upload_cams(P.cams.data(), V, dcams, s);
+    void* st_mut = const_cast<void*>(state);  // read only below; RecordArgs carries non-const pointers
+    const RecordArgs rec = record_args(st_mut, L);
+    float* rec_grad = at<float>(workspace, P.b_grad);
+    {
+        StageTimer t(MVGS_STAGE_ZERO_GRADS, s);
+        launch_zero_f32(rec_grad, (size_t)cap->records * kGradStride, s);
+    }
+
+    BlendArgs ba;
+    ba.cams = dcams;
+    ba.V = V;
+    ba.tw = cfg->tile_w;
+    ba.th = cfg->tile_h;
+    ba.tiles = P.tiles;
+    ba.ranges = at<long long>(state, L.off_tile_ranges);
+    ba.sorted = at<uint32_t>(state, L.off_sorted_records);
+    ba.xy = rec.xy;
+    ba.conic_o = rec.conic_o;
+    ba.rgb_r = rec.rgb_r;
+    for (int i = 0; i < 3; i++) ba.bg[i] = cfg->bg[i];
+    {
+        StageTimer t(MVGS_STAGE_BLEND_BACKWARD, s);
+        launch_blend_backward(ba, dL_dimages, at<float>(state, L.off_final_T), at<uint32_t>(state, L.off_n_contrib),
+                              rec_grad, s);
+    }
+    {
+        StageTimer t(MVGS_STAGE_PREPROCESS_BACKWARD, s);
+        launch_preprocess_backward(scene_args(scene), dcams, V, rec, rec_grad, g_means, g_log_scales, g_quats,
+                                   g_opacity_logits, g_sh, g_mean2d, e1, s);
+    }
+    return cuda_check("render backward");
+}
+
+size_t mvgs_dssim_workspace_size(const int32_t* hw, int32_t V) {
+    if (!hw || V < 1) return 0;
+    return dssim_temp_bytes(hw, V);
+}
+
+mvgs_status mvgs_dssim_loss(const float* img, const float* target, const int32_t* hw, int32_t V, float lambda,
+                            float* loss_per_view, float* dL_dimg, void* workspace, size_t workspace_bytes,
+                            mvgs_stream stream) {
+    if (!img || !target || !hw || !loss_per_view || !workspace) return fail(MVGS_EINVAL, "NULL argument");
+    if (V < 1) return fail(MVGS_EINVAL, "need at least one view");
+    for (int v = 0; v < V; v++)
+        if (hw[2 * v] < 1 || hw[2 * v + 1] < 1) return fail(MVGS_EINVAL, "view %d: empty image", v);
+    if (!(lambda >= 0.f && lambda <= 1.f)) return fail(MVGS_EINVAL, "lambda must be in [0, 1]");
+    const size_t need = dssim_temp_bytes(hw, V);
+    if (workspace_bytes < need) return fail(MVGS_ENOSPACE, "workspace %zu < %zu bytes", workspace_bytes, need);
+    {
+        StageTimer t(MVGS_STAGE_DSSIM, reinterpret_cast<cudaStream_t>(stream));
+        launch_dssim(img, target, hw, V, lambda, loss_per_view, dL_dimg, workspace,
+                     reinterpret_cast<cudaStream_t>(stream));
+    }
+    return cuda_check("dssim");
+}
+
+mvgs_status mvgs_adc_accumulate(const void* state, int64_t n, const float* g_mean2d, const float* e1,
+                                float* accum_e1, float* accum_e2, float* denom, mvgs_stream stream) {
+    if (!state || !g_mean2d || !e1 || !accum_e1 || !accum_e2 || !denom) return fail(MVGS_EINVAL, "NULL argument");
+    if (n < 0) return fail(MVGS_EINVAL, "n < 0");
+    // the record offsets sit right after the 256-byte count block of the state
+    const long long* rec_off = at<long long>(state, 256);
+    {
+        StageTimer t(MVGS_STAGE_ADC, reinterpret_cast<cudaStream_t>(stream));
+        launch_adc_accumulate(rec_off, n, g_mean2d, e1, accum_e1, accum_e2, denom,
+                              reinterpret_cast<cudaStream_t>(stream));
+    }
+    return cuda_check("adc");
+}
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+// Shared definitions of the sm_103a kernels (device side of libmvgs).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mvgs {
+
+// Rasterizer constants the paper inherits from 3DGS without printing them
+// (Sec. 3 cites the 3DGS rasterizer and EWA splatting): low-pass dilation of
+// the projected covariance, alpha clamp, alpha skip threshold, transmittance
+// cutoff, guard band of the projection Jacobian, 3-sigma radius and the
+// eigenvalue floor used for it.
+constexpr float kDilation = 0.3f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTMin = 1e-4f;
+constexpr float kGuard = 1.3f;
+constexpr float kSigmas = 3.0f;
+constexpr float kEigFloor = 0.1f;
+
+// Per-view camera table entry, built on the host from mvgs_camera and
+// uploaded once per call; every kernel reads it from global memory.
+struct __align__(16) DevCam {
+    float R[9];      // world -> camera rotation, row-major
+    float t[3];
+    float fx, fy, cx, cy;
+    float campos[3];
+    float near_z;
+    float limx, limy;  // guard band on x/z and y/z
+    int W, H, tiles_x, tiles_y;
+    long long tile_base;  // first global tile id of the view
+    long long pix_base;   // first pixel of the view in the packed layout
+};
+
+constexpr int kCamChunk = 32;
+struct CamChunk {
+    DevCam c[kCamChunk];
+};
+
+// Per-record gradient slots written by the blend backward and read by the
+// preprocessing backward: mean2d (2), conic A B C (3), opacity (1), rgb (3),
+// E_1 term (1), padding (2).
+constexpr int kGradStride = 12;
+
+// Global tile ids index the view-major list of (view, tile) pairs.
+__device__ __forceinline__ int find_view(const DevCam* cams, int V, long long gt) {
+    int lo = 0, hi = V - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (cams[mid].tile_base <= gt) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The blend decision and opacity of one (pixel, Gaussian) pair (Eq. 1 with
+// the 3DGS clamp and skip rules).  Returns false when the Gaussian does not
+// take part at this pixel; otherwise alpha and the Gaussian falloff G.  The
+// forward and the backward call this same function so both take the same
+// branch for every pair.
+__device__ __forceinline__ bool pair_alpha(float dx, float dy, float4 co, float radius, float& alpha, float& G) {
+    if (fabsf(dx) > radius || fabsf(dy) > radius) return false;
+    const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
+    if (power > 0.f) return false;
+    G = __expf(power);
+    alpha = fminf(kAlphaMax, co.w * G);
+    return alpha >= kAlphaMin;
+}
+
+}  // namespace mvgs

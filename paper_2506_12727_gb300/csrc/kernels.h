@@ -1,0 +1,103 @@
+// Host-side launchers of the sm_103a kernels (internal to libmvgs).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace mvgs {
+
+// Process-wide count of kernels launched by the library (api.cu).
+void note_launches(int k);
+
+// ---- preprocess.cu -------------------------------------------------------
+void upload_cams(const DevCam* host, int V, DevCam* dst, cudaStream_t s);
+
+struct SceneArgs {
+    long long n;
+    int sh_degree;
+    const float* means;
+    const float* log_scales;
+    const float* quats;
+    const float* logits;
+    const float* sh;
+};
+
+// Records of the visible (Gaussian, view) pairs, Gaussian-major.
+struct RecordArgs {
+    long long* rec_off;  // [n + 1]
+    int* rec_g;
+    int* rec_v;
+    float2* xy;
+    float4* conic_o;
+    float4* rgb_r;       // rgb, radius
+    int* clamp;
+    float* depth;
+    short4* rect;
+};
+
+// vis: [n * V] bytes, 1 where (g, v) is visible; counts: visible views per Gaussian.
+void launch_count_visible(const SceneArgs& sc, const DevCam* cams, int V, int tw, int th, int* counts, uint8_t* vis,
+                          cudaStream_t s);
+// Writes all records of the visible pairs; also the depth-sort keys (float
+// bits of the depth), the identity permutation, and the number of tiles each
+// record touches.
+void launch_preprocess(const SceneArgs& sc, const DevCam* cams, int V, int tw, int th, const uint8_t* vis,
+                       const RecordArgs& rec, uint32_t* depth_keys, uint32_t* rec_ids, uint32_t* tiles_touched,
+                       cudaStream_t s);
+void launch_zero_f32(float* p, size_t count, cudaStream_t s);
+void launch_preprocess_backward(const SceneArgs& sc, const DevCam* cams, int V, const RecordArgs& rec,
+                                const float* rec_grad, float* g_means, float* g_log_scales, float* g_quats,
+                                float* g_logits, float* g_sh, float* out_mean2d, float* out_e1, cudaStream_t s);
+void launch_adc_accumulate(const long long* rec_off, long long n, const float* g_mean2d, const float* e1,
+                           float* accum_e1, float* accum_e2, float* denom, cudaStream_t s);
+
+// ---- sort.cu ---------------------------------------------------------------
+size_t scan_temp_bytes(uint64_t n);
+// out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
+void scan_i32_to_i64(const int* in, long long* out, uint64_t n, void* tmp, cudaStream_t s);
+void scan_u32_to_u64(const uint32_t* in, unsigned long long* out, uint64_t n, void* tmp, cudaStream_t s);
+// gathered variant: scans in[idx[i]]
+void scan_gather_u32_to_u64(const uint32_t* in, const uint32_t* idx, unsigned long long* out, uint64_t n, void* tmp,
+                            cudaStream_t s);
+
+size_t radix_temp_bytes(uint64_t n);
+// Stable LSD sort of (key, value) pairs on key bits [0, bits).  Input in
+// (keys_a, vals_a); buffers _b are scratch; the sorted values end in
+// vals_out and the sorted keys in *keys_sorted (one of keys_a / keys_b).
+void radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b, uint32_t* vals_out,
+                      uint32_t** keys_sorted, uint64_t n, int bits, void* tmp, cudaStream_t s);
+
+// One key per (record, covered tile), in the order of `order` (records sorted
+// by depth); tile_off is the exclusive scan of the tile counts in that order.
+void launch_duplicate(const uint32_t* order, const unsigned long long* tile_off, uint64_t R, uint64_t K,
+                      const short4* rect, const int* rec_v, const DevCam* cams, long long tiles, uint32_t* keys,
+                      uint32_t* vals, cudaStream_t s);
+void launch_tile_ranges(const uint32_t* sorted_keys, uint64_t K, long long* ranges, long long tiles,
+                        cudaStream_t s);
+
+// ---- blend.cu --------------------------------------------------------------
+struct BlendArgs {
+    const DevCam* cams;
+    int V;
+    int tw, th;
+    long long tiles;
+    const long long* ranges;
+    const uint32_t* sorted;
+    const float2* xy;
+    const float4* conic_o;
+    const float4* rgb_r;
+    float bg[3];
+};
+void launch_blend_forward(const BlendArgs& a, float* img, float* final_T, uint32_t* n_contrib, cudaStream_t s);
+void launch_blend_backward(const BlendArgs& a, const float* dimg, const float* final_T, const uint32_t* n_contrib,
+                           float* rec_grad, cudaStream_t s);
+
+// ---- dssim.cu --------------------------------------------------------------
+size_t dssim_temp_bytes(const int* hw, int V);
+void launch_dssim(const float* img, const float* target, const int* hw, int V, float lambda, float* loss_per_view,
+                  float* dimg, void* tmp, cudaStream_t s);
+
+}  // namespace mvgs

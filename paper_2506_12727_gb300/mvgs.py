@@ -1,0 +1,300 @@
+"""ctypes binding of libmvgs (include/mvgs.h) with the same call names.
+
+Argument marshalling only: torch tensors are passed as raw device pointers
+and the current CUDA stream; every step of the computation runs in the
+library's kernels.  Importing this module raises if the library has not been
+built -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+OK, EINVAL, ENOSPACE, EOVERFLOW, ECUDA, EDEVICE = 0, 1, 2, 3, 4, 5
+GRAD_STRIDE = 12
+
+
+class MvgsError(RuntimeError):
+    def __init__(self, status, msg, needed=None):
+        super().__init__(f"mvgs status {status}: {msg}")
+        self.status = status
+        self.needed = needed
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("viewmat", ctypes.c_float * 12), ("campos", ctypes.c_float * 3), ("near_z", ctypes.c_float)]
+
+
+class Scene(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacity_logits", ctypes.c_void_p), ("sh", ctypes.c_void_p)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("bg", ctypes.c_float * 3),
+                ("flags", ctypes.c_uint32)]
+
+
+class Capacity(ctypes.Structure):
+    _fields_ = [("records", ctypes.c_int64), ("keys", ctypes.c_int64)]
+
+
+_LAYOUT_FIELDS = ["state_bytes", "workspace_bytes", "off_counts", "off_rec_offsets", "off_rec_gauss", "off_rec_view",
+                  "off_rec_xy", "off_rec_conic_opacity", "off_rec_rgb", "off_rec_clamp", "off_rec_depth",
+                  "off_rec_rect", "off_sorted_records", "off_tile_ranges", "off_final_T", "off_n_contrib"]
+
+
+class Layout(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_size_t) for f in _LAYOUT_FIELDS] + [("tiles", ctypes.c_int64),
+                                                                 ("pixels", ctypes.c_int64)]
+
+
+# every symbol declared in include/mvgs.h
+EXPORTS = ["mvgs_render_layout", "mvgs_render_views", "mvgs_render_views_backward", "mvgs_dssim_workspace_size",
+           "mvgs_dssim_loss", "mvgs_adc_accumulate", "mvgs_profile_enable", "mvgs_profile_read", "mvgs_stage_name",
+           "mvgs_launch_count", "mvgs_last_error"]
+
+
+def load_library(path: str | None = None):
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libmvgs is not built ({path}); run paper_2506_12727_gb300.build.build() -- "
+                          "there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    lib.mvgs_render_layout.argtypes = [I64, P, I32, P, P, P]
+    lib.mvgs_render_views.argtypes = [P, P, I32, P, P, P, P, SZ, P, SZ, P, P]
+    lib.mvgs_render_views_backward.argtypes = [P, P, I32, P, P, P, P, SZ, P, SZ, P, P, P, P, P, P, P, P]
+    lib.mvgs_dssim_workspace_size.argtypes = [P, I32]
+    lib.mvgs_dssim_workspace_size.restype = SZ
+    lib.mvgs_dssim_loss.argtypes = [P, P, P, I32, ctypes.c_float, P, P, P, SZ, P]
+    lib.mvgs_adc_accumulate.argtypes = [P, I64, P, P, P, P, P, P]
+    lib.mvgs_last_error.restype = ctypes.c_char_p
+    lib.mvgs_profile_enable.argtypes = [I32]
+    lib.mvgs_profile_enable.restype = ctypes.c_int
+    lib.mvgs_profile_read.argtypes = [P, P, I32]
+    lib.mvgs_profile_read.restype = I32
+    lib.mvgs_stage_name.argtypes = [I32]
+    lib.mvgs_stage_name.restype = ctypes.c_char_p
+    lib.mvgs_launch_count.argtypes = []
+    lib.mvgs_launch_count.restype = I64
+    for f in ("mvgs_render_layout", "mvgs_render_views", "mvgs_render_views_backward", "mvgs_dssim_loss",
+              "mvgs_adc_accumulate"):
+        getattr(lib, f).restype = ctypes.c_int
+    return lib
+
+
+_lib = load_library()
+
+
+def last_error() -> str:
+    return _lib.mvgs_last_error().decode()
+
+
+def _check(status, needed=None):
+    if status != OK:
+        raise MvgsError(status, last_error(), needed)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "tensors passed to libmvgs must be contiguous CUDA tensors"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_cameras(cams) -> ctypes.Array:
+    """Packs a synth.Cameras (numpy arrays) into an array of mvgs_camera."""
+    V = cams.V
+    arr = (Camera * V)()
+    for v in range(V):
+        c = arr[v]
+        c.width, c.height = int(cams.width[v]), int(cams.height[v])
+        c.fx, c.fy, c.cx, c.cy = float(cams.fx[v]), float(cams.fy[v]), float(cams.cx[v]), float(cams.cy[v])
+        c.viewmat[:] = [float(x) for x in np.asarray(cams.viewmat[v], np.float32).reshape(12)]
+        c.campos[:] = [float(x) for x in cams.campos[v]]
+        c.near_z = float(cams.near[v])
+    return arr
+
+
+def make_config(tile=(16, 16), bg=(0.0, 0.0, 0.0)) -> Config:
+    cfg = Config()
+    cfg.tile_w, cfg.tile_h = int(tile[0]), int(tile[1])
+    cfg.bg[:] = [float(b) for b in bg]
+    cfg.flags = 0
+    return cfg
+
+
+def make_scene(params: dict, sh_degree: int) -> Scene:
+    """`params`: dict of contiguous float32 CUDA tensors means, log_scales,
+    quats, opacity_logits, sh."""
+    sc = Scene()
+    sc.n = int(params["means"].shape[0])
+    sc.sh_degree = int(sh_degree)
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        t = params[k]
+        assert t.dtype == torch.float32
+        setattr(sc, k, _ptr(t))
+    return sc
+
+
+# ---------------------------------------------------------------------------
+# the C calls, one to one
+# ---------------------------------------------------------------------------
+def render_layout(n, cams_c, cfg, cap) -> Layout:
+    L = Layout()
+    _check(_lib.mvgs_render_layout(n, cams_c, len(cams_c), ctypes.byref(cfg), ctypes.byref(cap), ctypes.byref(L)))
+    return L
+
+
+def render_views(scene_c, cams_c, cfg, cap, images, state, workspace, stream=None):
+    """Returns the needed Capacity; raises MvgsError (with .needed) on failure."""
+    needed = Capacity()
+    st = _lib.mvgs_render_views(ctypes.byref(scene_c), cams_c, len(cams_c), ctypes.byref(cfg), ctypes.byref(cap),
+                                _ptr(images), _ptr(state), state.numel(), _ptr(workspace), workspace.numel(),
+                                ctypes.byref(needed), _stream(stream))
+    _check(st, needed)
+    return needed
+
+
+def render_views_backward(scene_c, cams_c, cfg, cap, dL_dimages, state, workspace, grads: dict, g_mean2d=None,
+                          e1=None, stream=None):
+    st = _lib.mvgs_render_views_backward(ctypes.byref(scene_c), cams_c, len(cams_c), ctypes.byref(cfg),
+                                         ctypes.byref(cap), _ptr(dL_dimages), _ptr(state), state.numel(),
+                                         _ptr(workspace), workspace.numel(), _ptr(grads["means"]),
+                                         _ptr(grads["log_scales"]), _ptr(grads["quats"]),
+                                         _ptr(grads["opacity_logits"]), _ptr(grads["sh"]), _ptr(g_mean2d), _ptr(e1),
+                                         _stream(stream))
+    _check(st)
+
+
+def dssim_workspace_size(hw: np.ndarray) -> int:
+    hw = np.ascontiguousarray(hw, dtype=np.int32)
+    return int(_lib.mvgs_dssim_workspace_size(hw.ctypes.data_as(ctypes.c_void_p), hw.shape[0]))
+
+
+def dssim_loss(img, target, hw, lam, loss_per_view, dL_dimg, workspace, stream=None):
+    hw = np.ascontiguousarray(hw, dtype=np.int32)
+    st = _lib.mvgs_dssim_loss(_ptr(img), _ptr(target), hw.ctypes.data_as(ctypes.c_void_p), hw.shape[0],
+                              ctypes.c_float(lam), _ptr(loss_per_view), _ptr(dL_dimg), _ptr(workspace),
+                              workspace.numel(), _stream(stream))
+    _check(st)
+
+
+def adc_accumulate(state, n, g_mean2d, e1, accum_e1, accum_e2, denom, stream=None):
+    _check(_lib.mvgs_adc_accumulate(_ptr(state), n, _ptr(g_mean2d), _ptr(e1), _ptr(accum_e1), _ptr(accum_e2),
+                                    _ptr(denom), _stream(stream)))
+
+
+def launch_count() -> int:
+    return int(_lib.mvgs_launch_count())
+
+
+def profile_enable(on: bool):
+    _check(_lib.mvgs_profile_enable(1 if on else 0))
+
+
+def profile_read() -> dict:
+    """{stage name: (total ms, launches)} since the last read (waits for the events)."""
+    n = 32
+    ms = (ctypes.c_float * n)()
+    cnt = (ctypes.c_int64 * n)()
+    k = _lib.mvgs_profile_read(ms, cnt, n)
+    return {_lib.mvgs_stage_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(k)}
+
+
+# ---------------------------------------------------------------------------
+# buffer management around the calls
+# ---------------------------------------------------------------------------
+class Rasterizer:
+    """Keeps the caller-owned state and workspace buffers of one scene size
+    and camera set, growing them (with headroom) when a batch needs more
+    records or keys than the current capacity."""
+
+    def __init__(self, cams, tile=(16, 16), bg=(0.0, 0.0, 0.0), device="cuda", headroom=1.15):
+        self.cams_np = cams
+        self.cams_c = make_cameras(cams)
+        self.cfg = make_config(tile, bg)
+        self.device = device
+        self.headroom = headroom
+        self.cap = Capacity(0, 0)
+        self.state = None
+        self.workspace = None
+        self.layout = None
+        self.n = None
+        self.pixels = int(sum(int(w) * int(h) for w, h in zip(cams.width, cams.height)))
+        self.needed = Capacity(0, 0)
+
+    def _ensure(self, n, records, keys):
+        grow = self.state is None or n != self.n or records > self.cap.records or keys > self.cap.keys
+        if not grow:
+            return
+        cap = Capacity(max(int(records * self.headroom) + 1024, self.cap.records if n == self.n else 0),
+                       max(int(keys * self.headroom) + 4096, self.cap.keys if n == self.n else 0))
+        L = render_layout(n, self.cams_c, self.cfg, cap)
+        self.state = None
+        self.workspace = None
+        self.state = torch.empty(L.state_bytes, dtype=torch.uint8, device=self.device)
+        self.workspace = torch.empty(L.workspace_bytes, dtype=torch.uint8, device=self.device)
+        self.cap, self.layout, self.n = cap, L, n
+
+    def reserve(self, n, records, keys):
+        self._ensure(n, records, keys)
+
+    def forward(self, scene_c, images=None, stream=None):
+        n = scene_c.n
+        if images is None:
+            images = torch.empty(3 * self.pixels, dtype=torch.float32, device=self.device)
+        self._ensure(n, max(self.cap.records, 1), max(self.cap.keys, 1))
+        for _ in range(4):
+            try:
+                self.needed = render_views(scene_c, self.cams_c, self.cfg, self.cap, images, self.state,
+                                           self.workspace, stream)
+                return images
+            except MvgsError as e:
+                if e.status != ENOSPACE or e.needed is None:
+                    raise
+                self._ensure(n, max(e.needed.records, self.cap.records),
+                             max(e.needed.keys, self.cap.keys))
+        raise MvgsError(ENOSPACE, "could not size the buffers")
+
+    def backward(self, scene_c, dL_dimages, grads, g_mean2d=None, e1=None, stream=None):
+        render_views_backward(scene_c, self.cams_c, self.cfg, self.cap, dL_dimages, self.state, self.workspace,
+                              grads, g_mean2d, e1, stream)
+
+    # views into the state (intermediate results)
+    def _view(self, off, count, dtype, width=1):
+        nbytes = count * width * torch.tensor([], dtype=dtype).element_size()
+        t = self.state[off:off + nbytes].view(dtype)
+        return t.view(count, width) if width > 1 else t
+
+    def records(self) -> dict:
+        L = self.layout
+        R, K = int(self.needed.records), int(self.needed.keys)
+        return dict(
+            rec_off=self._view(L.off_rec_offsets, self.n + 1, torch.int64),
+            g=self._view(L.off_rec_gauss, R, torch.int32), v=self._view(L.off_rec_view, R, torch.int32),
+            xy=self._view(L.off_rec_xy, R, torch.float32, 2),
+            conic_o=self._view(L.off_rec_conic_opacity, R, torch.float32, 4),
+            rgb_r=self._view(L.off_rec_rgb, R, torch.float32, 4),
+            clamp=self._view(L.off_rec_clamp, R, torch.int32),
+            depth=self._view(L.off_rec_depth, R, torch.float32),
+            rect=self._view(L.off_rec_rect, R, torch.int16, 4),
+            sorted=self._view(L.off_sorted_records, K, torch.int32),
+            ranges=self._view(L.off_tile_ranges, int(L.tiles), torch.int64, 2),
+            final_T=self._view(L.off_final_T, int(L.pixels), torch.float32),
+            n_contrib=self._view(L.off_n_contrib, int(L.pixels), torch.int32),
+            counts=self._view(L.off_counts, 4, torch.int64))

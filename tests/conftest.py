@@ -19,6 +19,8 @@ def cuda_lib():
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
+    from paper_2506_12727_gb300 import build
+    build.build()
     from paper_2506_12727_gb300 import mvgs
     return mvgs
 

@@ -1,0 +1,58 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the C
+ABI on seeded inputs and lay its per-record outputs out like the oracle's
+dense (view, Gaussian) arrays."""
+import numpy as np
+import torch
+
+PARAMS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+def scene_to_device(scene, requires_grad=False):
+    return {k: torch.tensor(getattr(scene, k), dtype=torch.float32, device="cuda").contiguous() for k in PARAMS}
+
+
+def grads_like(params):
+    return {k: torch.empty_like(v) for k, v in params.items()}
+
+
+def gpu_forward(mvgs, scene, cams, tile=(16, 16), bg=(0.0, 0.0, 0.0), params=None):
+    params = params if params is not None else scene_to_device(scene)
+    sc = mvgs.make_scene(params, scene.sh_degree)
+    rz = mvgs.Rasterizer(cams, tile=tile, bg=bg)
+    img = rz.forward(sc)
+    torch.cuda.synchronize()
+    return rz, sc, params, img
+
+
+def dense_records(rz, N, V):
+    """GPU records scattered to dense [V*N] arrays (oracle layout)."""
+    rec = {k: v.cpu().numpy() for k, v in rz.records().items()}
+    idx = rec["v"].astype(np.int64) * N + rec["g"].astype(np.int64)
+    R = V * N
+    out = dict(valid=np.zeros(R, np.int32), xy=np.zeros((R, 2)), conic=np.zeros((R, 3)), opac=np.zeros(R),
+               rgb=np.zeros((R, 3)), radius=np.zeros(R, np.int32), depth=np.zeros(R), rect=np.zeros((R, 4), np.int32),
+               clamp=np.zeros(R, np.int32), rec_index=np.full(R, -1, np.int64))
+    out["valid"][idx] = 1
+    out["xy"][idx] = rec["xy"]
+    out["conic"][idx] = rec["conic_o"][:, :3]
+    out["opac"][idx] = rec["conic_o"][:, 3]
+    out["rgb"][idx] = rec["rgb_r"][:, :3]
+    out["radius"][idx] = rec["rgb_r"][:, 3].astype(np.int32)
+    out["depth"][idx] = rec["depth"]
+    out["rect"][idx] = rec["rect"]
+    out["clamp"][idx] = rec["clamp"]
+    out["rec_index"][idx] = np.arange(len(idx))
+    out["raw"] = rec
+    return out
+
+
+def assert_close_frac(got, ref, rtol, atol, what, max_bad=0):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    err = np.abs(got - ref)
+    bad = err > atol + rtol * np.abs(ref)
+    nb = int(bad.sum())
+    if nb > max_bad:
+        i = np.unravel_index(np.argmax(err - (atol + rtol * np.abs(ref))), err.shape)
+        raise AssertionError(f"{what}: {nb} of {err.size} entries outside tolerance (rtol={rtol}, atol={atol}); "
+                             f"worst at {i}: got {got[i]!r} ref {ref[i]!r}")
