@@ -89,8 +89,8 @@ typedef struct mvgs_scene {
 } mvgs_scene;
 
 /* Render settings.  tile_w x tile_h pixels form one tile; one CUDA block
- * renders one (tile, view).  Supported: tile_w, tile_h multiples of 8 with
- * 64 <= tile_w * tile_h <= 512 (8x8, 16x16, 16x32, ...).  The rendered
+ * renders one (tile, view).  Supported: tile_w and tile_h each 8, 16 or 32,
+ * with tile_w * tile_h <= 512 (8x8, 16x16, 16x32, 32x16, ...).  The rendered
  * image does not depend on the tile size: a pixel blends a Gaussian only when
  * it lies within the Gaussian's radius on both axes, and every tile that
  * holds such a pixel lists the Gaussian. */
@@ -204,9 +204,9 @@ typedef enum mvgs_stage {
     MVGS_STAGE_PREPROCESS,        /* projection, colour, radius, rect          */
     MVGS_STAGE_DEPTH_SORT,        /* records by depth                          */
     MVGS_STAGE_SCAN_TILES,        /* key offsets                               */
-    MVGS_STAGE_DUPLICATE,         /* one key per (record, tile)                */
-    MVGS_STAGE_TILE_SORT,         /* keys by (view, tile)                      */
-    MVGS_STAGE_RANGES,            /* per-tile list ranges                      */
+    MVGS_STAGE_TILE_SORT,         /* one entry per (record, tile), generated
+                                     in the first pass, sorted by (view, tile) */
+    MVGS_STAGE_RANGES,            /* per-tile list ranges from the rectangles  */
     MVGS_STAGE_BLEND_FORWARD,
     MVGS_STAGE_ZERO_GRADS,
     MVGS_STAGE_BLEND_BACKWARD,

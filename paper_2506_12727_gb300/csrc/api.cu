@@ -96,7 +96,7 @@ class StageTimer {
 };
 
 const char* kStageNames[MVGS_STAGE_COUNT] = {"count_visible", "scan_records", "preprocess", "depth_sort",
-                                             "scan_tiles", "duplicate", "tile_sort", "ranges", "blend_forward",
+                                             "scan_tiles", "tile_sort", "ranges", "blend_forward",
                                              "zero_grads", "blend_backward", "preprocess_backward", "dssim", "adc"};
 
 // Sub-allocation of one caller buffer.
@@ -118,7 +118,7 @@ struct Plan {
     // workspace offsets (forward)
     size_t w_cams = 0, w_counts = 0, w_vis = 0, w_scan = 0, w_dkeys_a = 0, w_dkeys_b = 0, w_ids_a = 0, w_ids_b = 0,
            w_order = 0, w_tiles = 0, w_tile_off = 0, w_keys_a = 0, w_keys_b = 0, w_vals_a = 0, w_vals_b = 0,
-           w_radix = 0;
+           w_radix = 0, w_tcount = 0;
     // workspace offsets (backward)
     size_t b_cams = 0, b_grad = 0;
 };
@@ -126,8 +126,9 @@ struct Plan {
 mvgs_status check_config(const mvgs_config* cfg) {
     if (!cfg) return fail(MVGS_EINVAL, "config is NULL");
     const int tw = cfg->tile_w, th = cfg->tile_h;
-    if (tw < 8 || th < 8 || tw % 8 || th % 8 || tw * th > 512 || tw * th < 64)
-        return fail(MVGS_EINVAL, "unsupported tile %dx%d (multiples of 8, 64..512 pixels)", tw, th);
+    const bool side_ok = (tw == 8 || tw == 16 || tw == 32) && (th == 8 || th == 16 || th == 32);
+    if (!side_ok || tw * th > 512)
+        return fail(MVGS_EINVAL, "unsupported tile %dx%d (sides 8, 16 or 32, at most 512 pixels)", tw, th);
     if (cfg->flags != 0) return fail(MVGS_EINVAL, "flags must be 0");
     return MVGS_OK;
 }
@@ -146,7 +147,7 @@ mvgs_status make_plan(long long n, const mvgs_camera* cams, int V, const mvgs_co
     P.V = V;
     P.n = n;
     P.cams.resize(V);
-    long long tiles = 0, pixels = 0;
+    long long tiles = 0, pixels = 0, cells = 0;
     for (int v = 0; v < V; v++) {
         const mvgs_camera& c = cams[v];
         if (c.width < 1 || c.height < 1) return fail(MVGS_EINVAL, "view %d: empty image", v);
@@ -167,6 +168,8 @@ mvgs_status make_plan(long long n, const mvgs_camera* cams, int V, const mvgs_co
         d.tiles_x = txs; d.tiles_y = tys;
         d.tile_base = tiles;
         d.pix_base = pixels;
+        d.diff_base = cells;
+        cells += (long long)(txs + 1) * (tys + 1);
         tiles += (long long)txs * tys;
         pixels += (long long)c.width * c.height;
     }
@@ -214,6 +217,7 @@ mvgs_status make_plan(long long n, const mvgs_camera* cams, int V, const mvgs_co
     P.w_vals_a = w.take(K * sizeof(uint32_t));
     P.w_vals_b = w.take(K * sizeof(uint32_t));
     P.w_radix = w.take(radix_temp_bytes(big));
+    P.w_tcount = w.take(tile_count_temp_bytes(P.cams.data(), V, tiles));
     const size_t fwd_bytes = w.off;
     Carver b;
     P.b_cams = b.take((size_t)V * sizeof(DevCam));
@@ -390,11 +394,10 @@ mvgs_status mvgs_render_views(const mvgs_scene* scene, const mvgs_camera* cams, 
 
     // records by depth, then keys per covered tile in that order
     uint32_t* order = at<uint32_t>(workspace, P.w_order);
-    uint32_t* dkeys_sorted = nullptr;
     {
         StageTimer t(MVGS_STAGE_DEPTH_SORT, s);
         radix_sort_pairs(dkeys_a, ids_a, at<uint32_t>(workspace, P.w_dkeys_b), at<uint32_t>(workspace, P.w_ids_b),
-                         order, &dkeys_sorted, (uint64_t)R, 32, at<void>(workspace, P.w_radix), s);
+                         order, (uint64_t)R, 32, at<void>(workspace, P.w_radix), s);
     }
     unsigned long long* tile_off = at<unsigned long long>(workspace, P.w_tile_off);
     {
@@ -411,23 +414,19 @@ mvgs_status mvgs_render_views(const mvgs_scene* scene, const mvgs_camera* cams, 
     if ((long long)K > cap->keys)
         return fail(MVGS_ENOSPACE, "%llu keys exceed the capacity of %lld", K, (long long)cap->keys);
 
-    uint32_t* keys_a = at<uint32_t>(workspace, P.w_keys_a);
-    uint32_t* vals_a = at<uint32_t>(workspace, P.w_vals_a);
-    {
-        StageTimer t(MVGS_STAGE_DUPLICATE, s);
-        launch_duplicate(order, tile_off, (uint64_t)R, K, rec.rect, rec.rec_v, dcams, P.tiles, keys_a, vals_a, s);
-    }
     uint32_t* sorted = at<uint32_t>(state, L.off_sorted_records);
-    uint32_t* keys_sorted = nullptr;
     {
         StageTimer t(MVGS_STAGE_TILE_SORT, s);
-        radix_sort_pairs(keys_a, vals_a, at<uint32_t>(workspace, P.w_keys_b), at<uint32_t>(workspace, P.w_vals_b),
-                         sorted, &keys_sorted, K, bits_for(P.tiles), at<void>(workspace, P.w_radix), s);
+        tile_sort(order, tile_off, (uint64_t)R, K, rec.rect, rec.rec_v, dcams, P.tiles, bits_for(P.tiles),
+                  at<uint32_t>(workspace, P.w_keys_a), at<uint32_t>(workspace, P.w_vals_a),
+                  at<uint32_t>(workspace, P.w_keys_b), at<uint32_t>(workspace, P.w_vals_b), sorted,
+                  at<void>(workspace, P.w_radix), s);
     }
     long long* ranges = at<long long>(state, L.off_tile_ranges);
     {
         StageTimer t(MVGS_STAGE_RANGES, s);
-        launch_tile_ranges(keys_sorted, K, ranges, P.tiles, s);
+        tile_ranges_from_rects(rec.rect, rec.rec_v, (uint64_t)R, dcams, P.cams.data(), V, P.tiles, ranges,
+                               at<void>(workspace, P.w_tcount), s);
     }
     set_counts_kernel<<<1, 1, 0, s>>>(counts_dev, R, (long long)K, P.tiles, P.pixels);
     note_launches(1);

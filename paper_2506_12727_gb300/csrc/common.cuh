@@ -31,7 +31,9 @@ struct __align__(16) DevCam {
     int W, H, tiles_x, tiles_y;
     long long tile_base;  // first global tile id of the view
     long long pix_base;   // first pixel of the view in the packed layout
+    long long diff_base;  // first cell of the view's (tiles_y + 1) x (tiles_x + 1) count grid
 };
+static_assert(sizeof(DevCam) == 128, "camera table entry is 128 bytes");
 
 constexpr int kCamChunk = 32;
 struct CamChunk {

@@ -65,18 +65,25 @@ void scan_gather_u32_to_u64(const uint32_t* in, const uint32_t* idx, unsigned lo
 
 size_t radix_temp_bytes(uint64_t n);
 // Stable LSD sort of (key, value) pairs on key bits [0, bits).  Input in
-// (keys_a, vals_a); buffers _b are scratch; the sorted values end in
-// vals_out and the sorted keys in *keys_sorted (one of keys_a / keys_b).
+// (keys_a, vals_a), which are overwritten; buffers _b are scratch; the sorted
+// values end in vals_out.
 void radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b, uint32_t* vals_out,
-                      uint32_t** keys_sorted, uint64_t n, int bits, void* tmp, cudaStream_t s);
+                      uint64_t n, int bits, void* tmp, cudaStream_t s);
 
-// One key per (record, covered tile), in the order of `order` (records sorted
-// by depth); tile_off is the exclusive scan of the tile counts in that order.
-void launch_duplicate(const uint32_t* order, const unsigned long long* tile_off, uint64_t R, uint64_t K,
-                      const short4* rect, const int* rec_v, const DevCam* cams, long long tiles, uint32_t* keys,
-                      uint32_t* vals, cudaStream_t s);
-void launch_tile_ranges(const uint32_t* sorted_keys, uint64_t K, long long* ranges, long long tiles,
-                        cudaStream_t s);
+// Stable sort, by global (view, tile) id, of one entry per (record, covered
+// tile) taken in the order of `order` (records sorted by depth); tile_off is
+// the exclusive scan of the records' tile counts in that order.  The entries
+// are generated inside the first radix pass.  Sorted record ids end in
+// vals_out; keys_a/b and vals_a/b are scratch of K entries.
+void tile_sort(const uint32_t* order, const unsigned long long* tile_off, uint64_t R, uint64_t K, const short4* rect,
+               const int* rec_v, const DevCam* cams, long long tiles, int bits, uint32_t* keys_a, uint32_t* vals_a,
+               uint32_t* keys_b, uint32_t* vals_b, uint32_t* vals_out, void* tmp, cudaStream_t s);
+
+// Per-tile [start, end) of the sorted list, from the records' rectangles.
+size_t tile_count_temp_bytes(const DevCam* host_cams, int V, long long tiles);
+void tile_ranges_from_rects(const short4* rect, const int* rec_v, uint64_t R, const DevCam* cams,
+                            const DevCam* host_cams, int V, long long tiles, long long* ranges, void* tmp,
+                            cudaStream_t s);
 
 // ---- blend.cu --------------------------------------------------------------
 struct BlendArgs {

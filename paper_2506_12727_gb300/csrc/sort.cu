@@ -9,6 +9,8 @@
 // instead of 32 + that.  Stability keeps depth order, and equal depths keep
 // the record order, which is Gaussian-major, so ties inside a tile list are
 // broken by Gaussian index.
+#include <cstddef>
+
 #include "kernels.h"
 
 namespace mvgs {
@@ -157,6 +159,90 @@ constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_SEG = RS_ITEMS * 32;  // contiguous keys per warp
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 
+struct RankSmem {
+    uint32_t whist[RS_WARPS * 256];  // per-warp digit counts, then per-warp prefixes
+    uint32_t boff[256];              // first output position of each digit of the block
+    uint32_t dstart[256];            // first block-local position of each digit
+    uint32_t scan_buf[33];
+    uint32_t skeys[RS_TILE];         // keys in block-local sorted order
+    uint32_t svals[RS_TILE + 1];     // values in block-local sorted order (+1: see dup_downsweep)
+};
+
+// Stable rank of the block's keys (held in registers, warp w owning the
+// contiguous segment [w*SEG, (w+1)*SEG) in rounds of 32 lanes) and scatter:
+// first into shared memory in block-local digit order, then to global memory
+// in runs of consecutive positions per digit.  Equal digits inside a round are
+// found with one ballot per digit bit.  Values are fetched after the ranking
+// (get_val(block-local index)), so they do not occupy registers during it.
+template <bool WRITE_KEYS, class GetVal>
+__device__ __forceinline__ void rank_and_scatter(RankSmem& sm, const uint32_t (&k)[RS_ITEMS], uint64_t n, int shift,
+                                                 const uint32_t* __restrict__ offsets, uint32_t nblocks,
+                                                 uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                 GetVal get_val) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint64_t block0 = (uint64_t)blockIdx.x * RS_TILE;
+    const int local0 = warp * RS_SEG + lane;
+    const uint64_t base = block0 + local0;
+    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) sm.whist[i] = 0;
+    sm.boff[threadIdx.x] = offsets[(uint64_t)threadIdx.x * nblocks + blockIdx.x];
+    __syncthreads();
+    uint32_t* wh = sm.whist + warp * 256;
+    uint32_t lr[RS_ITEMS];
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; j++) {
+        const bool ok = base + (uint64_t)j * 32 < n;
+        const uint32_t d = (k[j] >> shift) & 0xffu;
+        uint32_t peers = __ballot_sync(kFull, ok);
+#pragma unroll
+        for (int b = 0; b < 8; b++) {
+            const uint32_t bit = (d >> b) & 1u;
+            const uint32_t bb = __ballot_sync(kFull, bit);
+            peers &= bit ? bb : ~bb;
+        }
+        const uint32_t rank = __popc(peers & lt);
+        const uint32_t before = wh[d];
+        __syncwarp();
+        if (ok && rank == 0) wh[d] = before + __popc(peers);
+        __syncwarp();
+        lr[j] = before + rank;
+    }
+    // values are read before the barrier that precedes the scatter, so a
+    // source may keep them in the staging the scatter overwrites
+    uint32_t vv[RS_ITEMS];
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; j++) vv[j] = base + (uint64_t)j * 32 < n ? get_val(local0 + j * 32) : 0u;
+    __syncthreads();
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; w++) {
+        const uint32_t c = sm.whist[w * 256 + threadIdx.x];
+        sm.whist[w * 256 + threadIdx.x] = run;
+        run += c;
+    }
+    uint32_t total;
+    sm.dstart[threadIdx.x] = block_exclusive_scan<uint32_t>(run, sm.scan_buf, total);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; j++) {
+        if (base + (uint64_t)j * 32 < n) {
+            const uint32_t d = (k[j] >> shift) & 0xffu;
+            const uint32_t lp = sm.dstart[d] + wh[d] + lr[j];
+            sm.skeys[lp] = k[j];
+            sm.svals[lp] = vv[j];
+        }
+    }
+    __syncthreads();
+    const int cnt = (int)(n - block0 < (uint64_t)RS_TILE ? n - block0 : (uint64_t)RS_TILE);
+    for (int i = threadIdx.x; i < cnt; i += RS_THREADS) {
+        const uint32_t key = sm.skeys[i];
+        const uint32_t d = (key >> shift) & 0xffu;
+        const uint32_t pos = sm.boff[d] + (uint32_t)i - sm.dstart[d];
+        vout[pos] = sm.svals[i];
+        if (WRITE_KEYS) kout[pos] = key;
+    }
+}
+
 // Per-block digit histogram, stored digit-major so that one exclusive scan of
 // the whole table gives every block's first output position per digit.
 __global__ void __launch_bounds__(RS_THREADS) rs_upsweep(const uint32_t* __restrict__ keys, uint64_t n, int shift,
@@ -178,158 +264,224 @@ __global__ void __launch_bounds__(RS_THREADS) rs_upsweep(const uint32_t* __restr
     counts[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = sum;
 }
 
-// Stable scatter.  Warp w ranks the keys of its contiguous segment in index
-// order (32 per round, lanes in order); equal digits inside a round are found
-// with one ballot per digit bit.  Warps are then offset by the counts of the
-// warps before them, and the block by the scanned table.
-__global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t* __restrict__ kin,
-                                                          const uint32_t* __restrict__ vin,
-                                                          uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                                          uint64_t n, int shift, const uint32_t* __restrict__ offsets,
-                                                          uint32_t nblocks) {
-    __shared__ uint32_t whist[RS_WARPS * 256];
-    __shared__ uint32_t boff[256];
-    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) whist[i] = 0;
-    boff[threadIdx.x] = offsets[(uint64_t)threadIdx.x * nblocks + blockIdx.x];
-    __syncthreads();
+template <bool WRITE_KEYS>
+__global__ void __launch_bounds__(RS_THREADS, 2) rs_downsweep(const uint32_t* __restrict__ kin,
+                                                             const uint32_t* __restrict__ vin,
+                                                             uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                             uint64_t n, int shift,
+                                                             const uint32_t* __restrict__ offsets, uint32_t nblocks) {
+    __shared__ RankSmem sm;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t lt = (1u << lane) - 1u;
-    const uint64_t base = (uint64_t)blockIdx.x * RS_TILE + warp * RS_SEG + lane;
-    uint32_t k[RS_ITEMS], v[RS_ITEMS], lr[RS_ITEMS];
+    const uint64_t block0 = (uint64_t)blockIdx.x * RS_TILE;
+    const uint64_t base = block0 + warp * RS_SEG + lane;
+    uint32_t k[RS_ITEMS];
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; j++) {
         const uint64_t idx = base + (uint64_t)j * 32;
-        const bool ok = idx < n;
-        k[j] = ok ? kin[idx] : 0u;
-        v[j] = ok ? vin[idx] : 0u;
+        k[j] = idx < n ? kin[idx] : 0u;
     }
-    uint32_t* wh = whist + warp * 256;
-#pragma unroll
-    for (int j = 0; j < RS_ITEMS; j++) {
-        const bool ok = base + (uint64_t)j * 32 < n;
-        const uint32_t d = (k[j] >> shift) & 0xffu;
-        uint32_t peers = __ballot_sync(kFull, ok);
-#pragma unroll
-        for (int b = 0; b < 8; b++) {
-            const uint32_t bit = (d >> b) & 1u;
-            const uint32_t bb = __ballot_sync(kFull, bit);
-            peers &= bit ? bb : ~bb;
-        }
-        const uint32_t rank = __popc(peers & lt);
-        const uint32_t before = wh[d];
-        __syncwarp();
-        if (ok && rank == 0) wh[d] = before + __popc(peers);
-        __syncwarp();
-        lr[j] = before + rank;
-    }
-    __syncthreads();
-    {
-        uint32_t run = 0;
-#pragma unroll
-        for (int w = 0; w < RS_WARPS; w++) {
-            const uint32_t c = whist[w * 256 + threadIdx.x];
-            whist[w * 256 + threadIdx.x] = run;
-            run += c;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < RS_ITEMS; j++) {
-        if (base + (uint64_t)j * 32 < n) {
-            const uint32_t d = (k[j] >> shift) & 0xffu;
-            const uint32_t pos = boff[d] + wh[d] + lr[j];
-            kout[pos] = k[j];
-            vout[pos] = v[j];
-        }
-    }
+    rank_and_scatter<WRITE_KEYS>(sm, k, n, shift, offsets, nblocks, kout, vout,
+                                 [&](int local) { return vin[block0 + local]; });
 }
 
 // ---------------------------------------------------------------------------
-// duplication and tile ranges
+// keys generated from the depth-ordered records (duplication fused into the
+// first radix pass): key index k belongs to the record r with
+// off[r] <= k < off[r+1]; its tile is entry k - off[r] of the record's
+// rectangle in row-major order.
 // ---------------------------------------------------------------------------
-constexpr int DUP_THREADS = 256;
-constexpr int DUP_CHUNK = 2048;
+struct DupSrc {
+    const uint32_t* order;             // records by depth
+    const unsigned long long* off;     // [R + 1] exclusive scan of tiles in that order
+    uint64_t R;
+    const short4* rect;
+    const int* rec_v;
+    const DevCam* cams;
+    uint32_t tiles;
+};
 
-// Block b emits keys [b*CHUNK, (b+1)*CHUNK).  Each key finds its record by
-// a binary search over the (shared-memory) offsets of the records that cover
-// the chunk; consecutive threads write consecutive keys.
-__global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(const uint32_t* __restrict__ order,
-                                                               const unsigned long long* __restrict__ off,
-                                                               uint64_t R, uint64_t K, const short4* __restrict__ rect,
-                                                               const int* __restrict__ rec_v,
-                                                               const DevCam* __restrict__ cams, uint32_t tiles,
-                                                               uint32_t* __restrict__ keys,
-                                                               uint32_t* __restrict__ vals) {
-    __shared__ unsigned long long s_off[DUP_CHUNK + 1];
-    __shared__ unsigned long long s_lo;
-    __shared__ int s_n;
-    const uint64_t k0 = (uint64_t)blockIdx.x * DUP_CHUNK;
-    const uint64_t k1 = K < k0 + DUP_CHUNK ? K : k0 + DUP_CHUNK;
+// Finds the records covering keys [k0, k1) and stages their offsets (relative
+// to k0) in shared memory; nr < 0 when they do not fit (then keys search the
+// global offsets).
+__device__ __forceinline__ void dup_setup(const DupSrc& src, uint64_t k0, uint64_t k1, int* s_off,
+                                          unsigned long long* s_lo, int* s_n) {
     if (threadIdx.x == 0) {
-        // last record r with off[r] <= k0, then last with off[r] <= k1 - 1
-        uint64_t lo = 0, hi = R - 1;
+        uint64_t lo = 0, hi = src.R - 1;
         while (lo < hi) {
             const uint64_t mid = (lo + hi + 1) >> 1;
-            if (off[mid] <= k0) lo = mid; else hi = mid - 1;
+            if (src.off[mid] <= k0) lo = mid; else hi = mid - 1;
         }
         uint64_t lo2 = lo;
-        hi = R - 1;
+        hi = src.R - 1;
         while (lo2 < hi) {
             const uint64_t mid = (lo2 + hi + 1) >> 1;
-            if (off[mid] <= k1 - 1) lo2 = mid; else hi = mid - 1;
+            if (src.off[mid] <= k1 - 1) lo2 = mid; else hi = mid - 1;
         }
-        s_lo = lo;
-        // records with no tile share an offset with the next record, so a
-        // chunk can span more records than keys; those chunks search globally
-        s_n = lo2 - lo + 1 <= (uint64_t)DUP_CHUNK ? (int)(lo2 - lo + 1) : -1;
+        *s_lo = lo;
+        *s_n = lo2 - lo + 1 <= (uint64_t)RS_TILE ? (int)(lo2 - lo + 1) : -1;
     }
     __syncthreads();
-    const uint64_t rlo = s_lo;
-    const int nr = s_n;
-    if (nr > 0) {
-        for (int i = threadIdx.x; i <= nr; i += DUP_THREADS) s_off[i] = off[rlo + i];  // off has R + 1 entries
-    }
+    const int nr = *s_n;
+    const uint64_t rlo = *s_lo;
+    for (int i = threadIdx.x; i <= nr; i += blockDim.x) s_off[i] = (int)((long long)src.off[rlo + i] - (long long)k0);
     __syncthreads();
-    for (uint64_t k = k0 + threadIdx.x; k < k1; k += DUP_THREADS) {
-        uint64_t r;
-        unsigned long long first;
-        if (nr > 0) {
-            int lo = 0, hi = nr - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_off[mid] <= k) lo = mid; else hi = mid - 1;
-            }
-            r = rlo + lo;
-            first = s_off[lo];
-        } else {
-            uint64_t lo = 0, hi = R - 1;
-            while (lo < hi) {
-                const uint64_t mid = (lo + hi + 1) >> 1;
-                if (off[mid] <= k) lo = mid; else hi = mid - 1;
-            }
-            r = lo;
-            first = off[lo];
-        }
-        const uint32_t rec = order[r];
-        const uint32_t j = (uint32_t)(k - first);
-        const short4 rc = rect[rec];
-        const uint32_t w = (uint32_t)max(rc.z - rc.x, 1);
-        const uint32_t tx = rc.x + j % w, ty = rc.y + j / w;
-        const DevCam& cam = cams[rec_v[rec]];
-        const long long t = cam.tile_base + (long long)ty * cam.tiles_x + tx;
-        keys[k] = (uint32_t)(t < (long long)tiles ? t : (long long)tiles - 1);  // in range even for a bad record
-        vals[k] = rec;
-    }
 }
 
-__global__ void tile_ranges_kernel(const uint32_t* __restrict__ keys, uint64_t K, long long* __restrict__ ranges,
-                                   uint32_t tiles) {
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= K) return;
-    const uint32_t t = keys[i];
+__device__ __forceinline__ uint32_t dup_key(const DupSrc& src, const int* s_off, uint64_t rlo, int nr, uint64_t k0,
+                                            uint64_t k, uint32_t& val) {
+    uint64_t r;
+    long long first;
+    if (nr > 0) {
+        const int kk = (int)(k - k0);
+        int lo = 0, hi = nr - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= kk) lo = mid; else hi = mid - 1;
+        }
+        r = rlo + lo;
+        first = (long long)k0 + s_off[lo];
+    } else {
+        uint64_t lo = 0, hi = src.R - 1;
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi + 1) >> 1;
+            if (src.off[mid] <= k) lo = mid; else hi = mid - 1;
+        }
+        r = lo;
+        first = (long long)src.off[lo];
+    }
+    const uint32_t rec = src.order[r];
+    const uint32_t j = (uint32_t)((long long)k - first);
+    const short4 rc = src.rect[rec];
+    const uint32_t w = (uint32_t)max(rc.z - rc.x, 1);
+    const uint32_t tx = rc.x + j % w, ty = rc.y + j / w;
+    const DevCam& cam = src.cams[src.rec_v[rec]];
+    const long long t = cam.tile_base + (long long)ty * cam.tiles_x + tx;
+    val = rec;
+    return (uint32_t)(t < (long long)src.tiles ? t : (long long)src.tiles - 1);  // in range even for a bad record
+}
+
+__global__ void __launch_bounds__(RS_THREADS) dup_upsweep(DupSrc src, uint64_t K, int shift,
+                                                         uint32_t* __restrict__ counts, uint32_t nblocks) {
+    __shared__ uint32_t hist[RS_WARPS * 256];
+    __shared__ int s_off[RS_TILE + 1];
+    __shared__ unsigned long long s_lo;
+    __shared__ int s_n;
+    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) hist[i] = 0;
+    const uint64_t k0 = (uint64_t)blockIdx.x * RS_TILE;
+    const uint64_t k1 = K < k0 + RS_TILE ? K : k0 + RS_TILE;
+    dup_setup(src, k0, k1, s_off, &s_lo, &s_n);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t base = k0 + warp * RS_SEG + lane;
+    const uint64_t rlo = s_lo;
+    const int nr = s_n;
+#pragma unroll 4
+    for (int j = 0; j < RS_ITEMS; j++) {
+        const uint64_t idx = base + (uint64_t)j * 32;
+        if (idx < K) {
+            uint32_t val;
+            const uint32_t key = dup_key(src, s_off, rlo, nr, k0, idx, val);
+            atomicAdd(&hist[warp * 256 + ((key >> shift) & 0xffu)], 1u);
+        }
+    }
+    __syncthreads();
+    uint32_t sum = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; w++) sum += hist[w * 256 + threadIdx.x];
+    counts[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = sum;
+}
+
+template <bool WRITE_KEYS>
+__global__ void __launch_bounds__(RS_THREADS, 2) dup_downsweep(DupSrc src, uint64_t K, int shift,
+                                                              const uint32_t* __restrict__ offsets, uint32_t nblocks,
+                                                              uint32_t* __restrict__ kout,
+                                                              uint32_t* __restrict__ vout) {
+    __shared__ RankSmem sm;
+    __shared__ unsigned long long s_lo;
+    __shared__ int s_n;
+    const uint64_t k0 = (uint64_t)blockIdx.x * RS_TILE;
+    const uint64_t k1 = K < k0 + RS_TILE ? K : k0 + RS_TILE;
+    // until the scatter, the sorted staging holds the records' offsets (keys
+    // half, one entry spilling into the values half) and the generated values
+    // in block-local index order (values half, from entry 1)
+    int* s_off = reinterpret_cast<int*>(sm.skeys);
+    uint32_t* s_gval = sm.svals + 1;
+    static_assert(offsetof(RankSmem, svals) == offsetof(RankSmem, skeys) + RS_TILE * sizeof(uint32_t),
+                  "the offsets may run one entry into the values half");
+    static_assert(sizeof(sm.svals) >= (RS_TILE + 1) * sizeof(uint32_t), "values after the spilled offset fit");
+    dup_setup(src, k0, k1, s_off, &s_lo, &s_n);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int local0 = warp * RS_SEG + lane;
+    const uint64_t rlo = s_lo;
+    const int nr = s_n;
+    uint32_t k[RS_ITEMS];
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; j++) {
+        const uint64_t idx = k0 + local0 + (uint64_t)j * 32;
+        k[j] = 0u;
+        if (idx < K) {
+            uint32_t val;
+            k[j] = dup_key(src, s_off, rlo, nr, k0, idx, val);
+            s_gval[local0 + j * 32] = val;
+        }
+    }
+    // rank_and_scatter synchronises before it overwrites the staged offsets
+    rank_and_scatter<WRITE_KEYS>(sm, k, K, shift, offsets, nblocks, kout, vout,
+                                 [&](int local) { return s_gval[local]; });
+}
+
+// ---------------------------------------------------------------------------
+// per-tile list lengths from the records' rectangles (2D difference counts),
+// so the tile ranges need no pass over the sorted keys
+// ---------------------------------------------------------------------------
+__global__ void rect_diff_kernel(const short4* __restrict__ rect, const int* __restrict__ rec_v, uint64_t R,
+                                 const DevCam* __restrict__ cams, int* __restrict__ diff) {
+    const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const short4 rc = rect[r];
+    if (rc.z <= rc.x || rc.w <= rc.y) return;
+    const DevCam& cam = cams[rec_v[r]];
+    const long long W1 = cam.tiles_x + 1;
+    int* d = diff + cam.diff_base;
+    atomicAdd(d + rc.y * W1 + rc.x, 1);
+    atomicAdd(d + rc.y * W1 + rc.z, -1);
+    atomicAdd(d + rc.w * W1 + rc.x, -1);
+    atomicAdd(d + rc.w * W1 + rc.z, 1);
+}
+
+// One block per view: prefix sums along rows, then along columns, give the
+// number of records covering each tile.
+__global__ void diff_to_counts_kernel(const DevCam* __restrict__ cams, int* __restrict__ diff,
+                                      uint32_t* __restrict__ counts) {
+    const DevCam& cam = cams[blockIdx.x];
+    const int W1 = cam.tiles_x + 1, H1 = cam.tiles_y + 1;
+    int* d = diff + cam.diff_base;
+    for (int y = threadIdx.x; y < H1; y += blockDim.x) {
+        int run = 0;
+        for (int x = 0; x < W1; x++) {
+            run += d[y * W1 + x];
+            d[y * W1 + x] = run;
+        }
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < W1; x += blockDim.x) {
+        int run = 0;
+        for (int y = 0; y < H1; y++) {
+            run += d[y * W1 + x];
+            d[y * W1 + x] = run;
+        }
+    }
+    __syncthreads();
+    const int n = cam.tiles_x * cam.tiles_y;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        counts[cam.tile_base + i] = (uint32_t)d[(i / cam.tiles_x) * W1 + (i % cam.tiles_x)];
+}
+
+__global__ void ranges_kernel(const unsigned long long* __restrict__ starts, long long tiles,
+                              long long* __restrict__ ranges) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= tiles) return;
-    if (i == 0 || keys[i - 1] != t) ranges[2 * (uint64_t)t] = (long long)i;
-    if (i == K - 1 || keys[i + 1] != t) ranges[2 * (uint64_t)t + 1] = (long long)(i + 1);
+    ranges[2 * t] = (long long)starts[t];
+    ranges[2 * t + 1] = (long long)starts[t + 1];
 }
 
 }  // namespace
@@ -360,25 +512,40 @@ size_t radix_temp_bytes(uint64_t n) {
     return counts + scan_temp_bytes(256 * nb);
 }
 
+namespace {
+// One radix pass: histogram, scan, scatter.
+template <class Up, class Down>
+void radix_pass(uint64_t n, void* tmp, cudaStream_t s, Up up, Down down) {
+    const uint64_t nb = radix_blocks(n);
+    uint32_t* counts = static_cast<uint32_t*>(tmp);
+    void* scan_tmp = static_cast<char*>(tmp) + ((256 * nb * sizeof(uint32_t)) + 255) / 256 * 256;
+    up((unsigned)nb, counts);
+    scan_impl(LoadDirect<uint32_t, uint32_t>{counts}, counts, 256 * nb, (uint32_t*)nullptr, scan_tmp, s);
+    down((unsigned)nb, counts);
+    note_launches(2);
+}
+}  // namespace
+
 void radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b, uint32_t* vals_out,
-                      uint32_t** keys_sorted, uint64_t n, int bits, void* tmp, cudaStream_t s) {
-    *keys_sorted = keys_a;
+                      uint64_t n, int bits, void* tmp, cudaStream_t s) {
     if (n == 0) return;
     const int passes = (bits + 7) / 8;
     if (passes == 0) {
         cudaMemcpyAsync(vals_out, vals_a, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
         return;
     }
-    const uint64_t nb = radix_blocks(n);
-    uint32_t* counts = static_cast<uint32_t*>(tmp);
-    void* scan_tmp = static_cast<char*>(tmp) + ((256 * nb * sizeof(uint32_t)) + 255) / 256 * 256;
     uint32_t *kin = keys_a, *vin = vals_a, *kout = keys_b, *vout = vals_b;
     for (int p = 0; p < passes; p++) {
-        if (p == passes - 1) vout = vals_out;
-        rs_upsweep<<<(unsigned)nb, RS_THREADS, 0, s>>>(kin, n, 8 * p, counts, (uint32_t)nb);
-        scan_impl(LoadDirect<uint32_t, uint32_t>{counts}, counts, 256 * nb, (uint32_t*)nullptr, scan_tmp, s);
-        rs_downsweep<<<(unsigned)nb, RS_THREADS, 0, s>>>(kin, vin, kout, vout, n, 8 * p, counts, (uint32_t)nb);
-        note_launches(2);
+        const bool last = p == passes - 1;
+        if (last) vout = vals_out;
+        const int shift = 8 * p;
+        radix_pass(
+            n, tmp, s,
+            [&](unsigned nb, uint32_t* counts) { rs_upsweep<<<nb, RS_THREADS, 0, s>>>(kin, n, shift, counts, nb); },
+            [&](unsigned nb, uint32_t* counts) {
+                if (last) rs_downsweep<false><<<nb, RS_THREADS, 0, s>>>(kin, vin, kout, vout, n, shift, counts, nb);
+                else rs_downsweep<true><<<nb, RS_THREADS, 0, s>>>(kin, vin, kout, vout, n, shift, counts, nb);
+            });
         uint32_t* nk = kin;
         uint32_t* nv = vin;
         kin = kout;
@@ -386,24 +553,77 @@ void radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint
         kout = nk;
         vout = (nv == vals_a || nv == vals_b) ? nv : vals_a;
     }
-    *keys_sorted = kin;
 }
 
-void launch_duplicate(const uint32_t* order, const unsigned long long* tile_off, uint64_t R, uint64_t K,
-                      const short4* rect, const int* rec_v, const DevCam* cams, long long tiles, uint32_t* keys,
-                      uint32_t* vals, cudaStream_t s) {
+void tile_sort(const uint32_t* order, const unsigned long long* tile_off, uint64_t R, uint64_t K, const short4* rect,
+               const int* rec_v, const DevCam* cams, long long tiles, int bits, uint32_t* keys_a, uint32_t* vals_a,
+               uint32_t* keys_b, uint32_t* vals_b, uint32_t* vals_out, void* tmp, cudaStream_t s) {
     if (K == 0 || R == 0) return;
-    duplicate_kernel<<<(unsigned)ceil_div_u64(K, DUP_CHUNK), DUP_THREADS, 0, s>>>(order, tile_off, R, K, rect, rec_v,
-                                                                                  cams, (uint32_t)tiles, keys, vals);
-    note_launches(1);
+    const DupSrc src{order, tile_off, R, rect, rec_v, cams, (uint32_t)tiles};
+    const int passes = bits > 8 ? (bits + 7) / 8 : 1;
+    // pass 0 generates the keys from the records
+    {
+        const bool last = passes == 1;
+        uint32_t* vout = last ? vals_out : vals_a;
+        radix_pass(
+            K, tmp, s,
+            [&](unsigned nb, uint32_t* counts) { dup_upsweep<<<nb, RS_THREADS, 0, s>>>(src, K, 0, counts, nb); },
+            [&](unsigned nb, uint32_t* counts) {
+                if (last) dup_downsweep<false><<<nb, RS_THREADS, 0, s>>>(src, K, 0, counts, nb, keys_a, vout);
+                else dup_downsweep<true><<<nb, RS_THREADS, 0, s>>>(src, K, 0, counts, nb, keys_a, vout);
+            });
+    }
+    uint32_t *kin = keys_a, *vin = vals_a, *kout = keys_b, *vout = vals_b;
+    for (int p = 1; p < passes; p++) {
+        const bool last = p == passes - 1;
+        if (last) vout = vals_out;
+        const int shift = 8 * p;
+        radix_pass(
+            K, tmp, s,
+            [&](unsigned nb, uint32_t* counts) { rs_upsweep<<<nb, RS_THREADS, 0, s>>>(kin, K, shift, counts, nb); },
+            [&](unsigned nb, uint32_t* counts) {
+                if (last) rs_downsweep<false><<<nb, RS_THREADS, 0, s>>>(kin, vin, kout, vout, K, shift, counts, nb);
+                else rs_downsweep<true><<<nb, RS_THREADS, 0, s>>>(kin, vin, kout, vout, K, shift, counts, nb);
+            });
+        uint32_t* nk = kin;
+        uint32_t* nv = vin;
+        kin = kout;
+        vin = vout;
+        kout = nk;
+        vout = nv;
+    }
 }
 
-void launch_tile_ranges(const uint32_t* sorted_keys, uint64_t K, long long* ranges, long long tiles,
-                        cudaStream_t s) {
-    cudaMemsetAsync(ranges, 0, (size_t)tiles * 2 * sizeof(long long), s);
-    if (K == 0) return;
-    tile_ranges_kernel<<<(unsigned)ceil_div_u64(K, 256), 256, 0, s>>>(sorted_keys, K, ranges, (uint32_t)tiles);
-    note_launches(1);
+size_t tile_count_temp_bytes(const DevCam* host_cams, int V, long long tiles) {
+    long long cells = 0;
+    for (int v = 0; v < V; v++) cells += (long long)(host_cams[v].tiles_x + 1) * (host_cams[v].tiles_y + 1);
+    const size_t a = ((size_t)cells * sizeof(int) + 255) / 256 * 256;
+    const size_t b = ((size_t)tiles * sizeof(uint32_t) + 255) / 256 * 256;
+    const size_t c = ((size_t)(tiles + 1) * sizeof(unsigned long long) + 255) / 256 * 256;
+    return a + b + c + scan_temp_bytes((uint64_t)tiles);
+}
+
+void tile_ranges_from_rects(const short4* rect, const int* rec_v, uint64_t R, const DevCam* cams,
+                            const DevCam* host_cams, int V, long long tiles, long long* ranges, void* tmp,
+                            cudaStream_t s) {
+    long long cells = 0;
+    for (int v = 0; v < V; v++) cells += (long long)(host_cams[v].tiles_x + 1) * (host_cams[v].tiles_y + 1);
+    char* base = static_cast<char*>(tmp);
+    int* diff = reinterpret_cast<int*>(base);
+    base += ((size_t)cells * sizeof(int) + 255) / 256 * 256;
+    uint32_t* counts = reinterpret_cast<uint32_t*>(base);
+    base += ((size_t)tiles * sizeof(uint32_t) + 255) / 256 * 256;
+    unsigned long long* starts = reinterpret_cast<unsigned long long*>(base);
+    base += ((size_t)(tiles + 1) * sizeof(unsigned long long) + 255) / 256 * 256;
+    cudaMemsetAsync(diff, 0, (size_t)cells * sizeof(int), s);
+    if (R > 0) {
+        rect_diff_kernel<<<(unsigned)ceil_div_u64(R, 256), 256, 0, s>>>(rect, rec_v, R, cams, diff);
+        note_launches(1);
+    }
+    diff_to_counts_kernel<<<V, 256, 0, s>>>(cams, diff, counts);
+    scan_u32_to_u64(counts, starts, (uint64_t)tiles, base, s);
+    ranges_kernel<<<(unsigned)ceil_div_u64((uint64_t)tiles, 256), 256, 0, s>>>(starts, tiles, ranges);
+    note_launches(2);
 }
 
 }  // namespace mvgs

@@ -167,6 +167,9 @@ def workload(name: str):
     """Returns (scene, cameras, extras) for a named workload."""
     if name == "single_view_10k":
         return make_scene(10_000, 0), make_cameras([(128, 128)], radius=3.0), {"loss": "l1"}
+    if name == "multiview_500k_1x1264x832":  # one view of the batch below (profiling-sized)
+        return (make_scene(500_000, 3), make_cameras([(1264, 832)], radius=4.0),
+                {"loss": "l1_dssim", "lambda_dssim": 0.2})
     if name == "multiview_500k_4x1264x832":
         return (make_scene(500_000, 3), make_cameras([(1264, 832)] * 4, radius=4.0),
                 {"loss": "l1_dssim", "lambda_dssim": 0.2})

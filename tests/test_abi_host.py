@@ -62,7 +62,8 @@ def test_layout_is_aligned_and_consistent(lib):
 
 
 @pytest.mark.parametrize("tile,ok", [((16, 16), True), ((8, 8), True), ((16, 32), True), ((32, 16), True),
-                                     ((12, 16), False), ((4, 16), False), ((32, 32), False), ((8, 4), False)])
+                                     ((8, 32), True), ((12, 16), False), ((4, 16), False), ((32, 32), False),
+                                     ((8, 4), False), ((24, 8), False)])
 def test_tile_validation(lib, tile, ok):
     cams = lib.make_cameras(synth.make_cameras([(64, 64)]))
     if ok:

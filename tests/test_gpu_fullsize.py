@@ -1,0 +1,113 @@
+"""GPU parity at the benchmark's full size: 500k SH-3 Gaussians, 4 views of
+1264x832, 16x16 tiles, in the launch configuration bench.py times.
+
+The oracle cannot render the whole batch in seconds, so it checks
+  - sampled pixels of every view, each rendered on its own by the tile-free
+    per-pixel brute force over all Gaussians, and
+  - the full gradient of a loss that lives on a 64x64 window of each view:
+    the GPU runs the whole backward, the oracle only the window's pixels;
+    every Gaussian's gradient must agree.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_helpers import PARAMS, assert_close_frac, dense_records, gpu_forward, grads_like
+
+pytestmark = pytest.mark.gpu
+
+WORKLOAD = "multiview_500k_4x1264x832"
+TILE = (16, 16)
+
+
+@pytest.fixture(scope="module")
+def full(cuda_lib):
+    scene, cams, _ = synth.workload(WORKLOAD)
+    rz, sc, params, img = gpu_forward(cuda_lib, scene, cams, TILE)
+    return dict(scene=scene, cams=cams, rz=rz, sc=sc, params=params, img=img.cpu().numpy().astype(np.float64))
+
+
+def test_sampled_pixels_match_bruteforce(full):
+    scene, cams = full["scene"], full["cams"]
+    P = oracle.project(scene, cams, TILE)
+    rng = np.random.default_rng(51)
+    pix = []
+    for v in range(cams.V):
+        n = 250
+        pix.append(np.stack([np.full(n, v), rng.integers(0, cams.width[v], n), rng.integers(0, cams.height[v], n)], 1))
+    pix = np.concatenate(pix)
+    C, T, nc, amb = oracle.render_pixels_bruteforce(cams, P, pix)
+    _, _, _, pix_base = oracle.layout(cams, TILE)
+    img = full["img"]
+    got = np.zeros_like(C)
+    for i, (v, x, y) in enumerate(pix):
+        H, W = int(cams.height[v]), int(cams.width[v])
+        for ch in range(3):
+            got[i, ch] = img[3 * pix_base[v] + ch * H * W + y * W + x]
+    ok = (amb & oracle.PA_FORWARD) == 0
+    print(f"sampled pixels: {ok.mean():.2%} unambiguous, max |err| {np.abs(got - C)[ok].max():.3e}, "
+          f"mean contributors {nc.mean():.1f}")
+    assert ok.mean() > 0.95
+    assert_close_frac(got[ok], C[ok], 0, 1e-4, "sampled pixels")
+    rec = full["rz"].records()
+    Tg = rec["final_T"].cpu().numpy()
+    idx = np.array([pix_base[v] + y * cams.width[v] + x for v, x, y in pix])
+    assert_close_frac(Tg[idx][ok], T[ok], 0, 1e-4, "final T")
+
+
+def test_window_loss_gradients_match_oracle(full, cuda_lib):
+    scene, cams, rz = full["scene"], full["cams"], full["rz"]
+    rng = np.random.default_rng(52)
+    win = []
+    for v in range(cams.V):
+        x0 = int(rng.integers(0, cams.width[v] - 64))
+        y0 = int(rng.integers(0, cams.height[v] - 64))
+        win.append([x0, y0, x0 + 64, y0 + 64])
+    win = np.array(win, np.int32)
+    ref = oracle.forward(scene, cams, TILE, window=win)
+    _, _, _, pix_base = oracle.layout(cams, TILE)
+    dimg = np.zeros(3 * int(pix_base[-1]), np.float32)
+    for v in range(cams.V):
+        H, W = int(cams.height[v]), int(cams.width[v])
+        x0, y0, x1, y1 = win[v]
+        d = rng.normal(size=(3, 64, 64)).astype(np.float32)
+        amb = ref["amb"][pix_base[v]:pix_base[v + 1]].reshape(H, W)[y0:y1, x0:x1] != 0
+        d[:, amb] = 0.0
+        view = dimg[3 * pix_base[v]:3 * pix_base[v + 1]].reshape(3, H, W)
+        view[:, y0:y1, x0:x1] = d
+    # image parity on the windows too
+    img = full["img"]
+    for v in range(cams.V):
+        H, W = int(cams.height[v]), int(cams.width[v])
+        x0, y0, x1, y1 = win[v]
+        a = ref["amb"][pix_base[v]:pix_base[v + 1]].reshape(H, W)[y0:y1, x0:x1]
+        ok = (a & oracle.PA_FORWARD) == 0
+        g = img[3 * pix_base[v]:3 * pix_base[v + 1]].reshape(3, H, W)[:, y0:y1, x0:x1]
+        e = ref["img"][3 * pix_base[v]:3 * pix_base[v + 1]].reshape(3, H, W)[:, y0:y1, x0:x1]
+        assert_close_frac(g[:, ok], e[:, ok], 0, 1e-4, f"window image view {v}")
+    grads, g2d, e1 = oracle.backward(scene, cams, ref, dimg.astype(np.float64), TILE, window=win)
+    gg = grads_like(full["params"])
+    R = int(rz.needed.records)
+    gm2d = torch.zeros(R, 2, device="cuda")
+    ge1 = torch.zeros(R, device="cuda")
+    rz.backward(full["sc"], torch.tensor(dimg, device="cuda"), gg, gm2d, ge1)
+    torch.cuda.synchronize()
+    bad_g = np.zeros(scene.n, bool)
+    bad_g[np.nonzero(ref["P"]["amb"])[0] % scene.n] = True
+    touched = np.abs(grads["opacity_logits"]) > 0
+    print(f"window gradients: {touched.sum()} Gaussians touched, {bad_g.sum()} excluded")
+    assert touched.sum() > 1000
+    for k in PARAMS:
+        got = gg[k].cpu().numpy().astype(np.float64)[~bad_g]
+        exp = grads[k][~bad_g]
+        floor = 1e-5 * np.abs(exp).max()
+        err = np.abs(got - exp) / (np.abs(exp) + floor)
+        print(f"d{k}: max rel err {err.max():.3e}, p99 {np.quantile(err[touched[~bad_g]], 0.99):.3e}")
+        assert_close_frac(got, exp, 1e-3, floor, "d" + k)
+    D = dense_records(rz, scene.n, cams.V)
+    vis = (D["valid"] != 0) & ~bad_g[np.arange(scene.n * cams.V) % scene.n]
+    gm = np.zeros((scene.n * cams.V, 2))
+    gm[D["valid"] != 0] = gm2d.cpu().numpy()[D["rec_index"][D["valid"] != 0]]
+    assert_close_frac(gm[vis], g2d[vis, :2], 1e-3, 1e-5 * np.abs(g2d[:, :2]).max(), "mean2d")
