@@ -126,6 +126,7 @@ typedef struct mvgs_layout {
     size_t off_rec_rect;             /* int16x4[records]: tile x0, y0, x1, y1 (excl.) */
     size_t off_sorted_records;       /* uint32[keys]: record ids sorted by (view, tile, depth, Gaussian) */
     size_t off_tile_ranges;          /* int64x2[tiles]: [start, end) into the sorted ids */
+    size_t off_tile_order;           /* uint32[tiles]: blend processing order (longest lists first) */
     size_t off_final_T;              /* float[pixels]: transmittance after blending */
     size_t off_n_contrib;            /* uint32[pixels]: list position one past the last contributor */
     int64_t tiles;                   /* total tiles over all views                 */

@@ -118,9 +118,9 @@ struct Plan {
     // workspace offsets (forward)
     size_t w_cams = 0, w_counts = 0, w_vis = 0, w_scan = 0, w_dkeys_a = 0, w_dkeys_b = 0, w_ids_a = 0, w_ids_b = 0,
            w_order = 0, w_tiles = 0, w_tile_off = 0, w_keys_a = 0, w_keys_b = 0, w_vals_a = 0, w_vals_b = 0,
-           w_radix = 0, w_tcount = 0;
+           w_radix = 0, w_tcount = 0, w_torder = 0, w_counter = 0;
     // workspace offsets (backward)
-    size_t b_cams = 0, b_grad = 0;
+    size_t b_cams = 0, b_grad = 0, b_counter = 0;
 };
 
 mvgs_status check_config(const mvgs_config* cfg) {
@@ -193,6 +193,7 @@ mvgs_status make_plan(long long n, const mvgs_camera* cams, int V, const mvgs_co
     L.off_rec_rect = s.take(R * sizeof(short4));
     L.off_sorted_records = s.take(K * sizeof(uint32_t));
     L.off_tile_ranges = s.take((size_t)tiles * 2 * sizeof(long long));
+    L.off_tile_order = s.take((size_t)tiles * sizeof(uint32_t));
     L.off_final_T = s.take((size_t)pixels * sizeof(float));
     L.off_n_contrib = s.take((size_t)pixels * sizeof(uint32_t));
     L.state_bytes = s.off;
@@ -218,10 +219,13 @@ mvgs_status make_plan(long long n, const mvgs_camera* cams, int V, const mvgs_co
     P.w_vals_b = w.take(K * sizeof(uint32_t));
     P.w_radix = w.take(radix_temp_bytes(big));
     P.w_tcount = w.take(tile_count_temp_bytes(P.cams.data(), V, tiles));
+    P.w_torder = w.take(tile_order_temp_bytes(tiles));
+    P.w_counter = w.take(sizeof(int));
     const size_t fwd_bytes = w.off;
     Carver b;
     P.b_cams = b.take((size_t)V * sizeof(DevCam));
     P.b_grad = b.take(R * kGradStride * sizeof(float));
+    P.b_counter = b.take(sizeof(int));
     L.workspace_bytes = fwd_bytes > b.off ? fwd_bytes : b.off;
     return MVGS_OK;
 }
@@ -427,6 +431,7 @@ mvgs_status mvgs_render_views(const mvgs_scene* scene, const mvgs_camera* cams, 
         StageTimer t(MVGS_STAGE_RANGES, s);
         tile_ranges_from_rects(rec.rect, rec.rec_v, (uint64_t)R, dcams, P.cams.data(), V, P.tiles, ranges,
                                at<void>(workspace, P.w_tcount), s);
+        tile_order(ranges, P.tiles, at<uint32_t>(state, L.off_tile_order), at<void>(workspace, P.w_torder), s);
     }
     set_counts_kernel<<<1, 1, 0, s>>>(counts_dev, R, (long long)K, P.tiles, P.pixels);
     note_launches(1);
@@ -438,6 +443,7 @@ mvgs_status mvgs_render_views(const mvgs_scene* scene, const mvgs_camera* cams, 
     ba.th = th;
     ba.tiles = P.tiles;
     ba.ranges = ranges;
+    ba.order = at<uint32_t>(state, L.off_tile_order);
     ba.sorted = sorted;
     ba.xy = rec.xy;
     ba.conic_o = rec.conic_o;
@@ -445,7 +451,8 @@ mvgs_status mvgs_render_views(const mvgs_scene* scene, const mvgs_camera* cams, 
     for (int i = 0; i < 3; i++) ba.bg[i] = cfg->bg[i];
     {
         StageTimer t(MVGS_STAGE_BLEND_FORWARD, s);
-        launch_blend_forward(ba, images, at<float>(state, L.off_final_T), at<uint32_t>(state, L.off_n_contrib), s);
+        launch_blend_forward(ba, at<int>(workspace, P.w_counter), images, at<float>(state, L.off_final_T),
+                             at<uint32_t>(state, L.off_n_contrib), s);
     }
     return cuda_check("render");
 }
@@ -486,6 +493,7 @@ mvgs_status mvgs_render_views_backward(const mvgs_scene* scene, const mvgs_camer
     ba.th = cfg->tile_h;
     ba.tiles = P.tiles;
     ba.ranges = at<long long>(state, L.off_tile_ranges);
+    ba.order = at<uint32_t>(state, L.off_tile_order);
     ba.sorted = at<uint32_t>(state, L.off_sorted_records);
     ba.xy = rec.xy;
     ba.conic_o = rec.conic_o;
@@ -493,8 +501,8 @@ mvgs_status mvgs_render_views_backward(const mvgs_scene* scene, const mvgs_camer
     for (int i = 0; i < 3; i++) ba.bg[i] = cfg->bg[i];
     {
         StageTimer t(MVGS_STAGE_BLEND_BACKWARD, s);
-        launch_blend_backward(ba, dL_dimages, at<float>(state, L.off_final_T), at<uint32_t>(state, L.off_n_contrib),
-                              rec_grad, s);
+        launch_blend_backward(ba, at<int>(workspace, P.b_counter), dL_dimages, at<float>(state, L.off_final_T),
+                              at<uint32_t>(state, L.off_n_contrib), rec_grad, s);
     }
     {
         StageTimer t(MVGS_STAGE_PREPROCESS_BACKWARD, s);

@@ -1,24 +1,30 @@
 // Tile-based alpha blending (Eq. 1) and its backward.
 //
-// One block renders one (tile, view) pair: the supplement allocates "one block
-// for each viewpoint" per tile, and Alg. 2 has the block's threads fetch the
-// tile's depth-sorted Gaussians into shared memory batch by batch, blend, and
-// synchronise.  The whole batch of views is a single launch over the global
-// (view, tile) list, whatever the views' resolutions.
+// One block renders one (tile, view) pair at a time: the supplement allocates
+// "one block for each viewpoint" per tile, and Alg. 2 has the block's threads
+// fetch the tile's depth-sorted Gaussians into shared memory batch by batch,
+// blend, and synchronise.  The whole batch of views is a single persistent
+// launch over the global (view, tile) list, whatever the views' resolutions:
+// resident blocks take tiles from a queue in an order that puts the longest
+// lists first, so the heavy tiles do not form a tail.
 //
 // Each thread owns PPT pixels of one tile column (rows ly0, ly0 + R, ...), so
-// one shared-memory read of a Gaussian serves PPT pixels and, in the backward,
-// PPT per-pixel gradients are summed in registers before the warp reduction.
+// one shared-memory read of a Gaussian serves PPT pixels, and the per-pixel
+// updates are branch-free so the PPT dependency chains interleave.
 //
 // Forward per pixel (front to back): alpha = min(0.99, o G), skip alpha <
 // 1/255, stop before T (1 - alpha) < 1e-4, C += c alpha T, T *= 1 - alpha;
-// output C + T bg.  The block leaves the loop once every pixel has stopped.
+// output C + T bg.  A block leaves a tile once all its pixels have stopped.
 //
 // Backward per pixel (back to front from the last contributor), with T
 // recovered by division:  dC/dc_i = alpha_i T_i,  dC/dalpha_i = c_i T_i -
 // S_i / (1 - alpha_i), S_i the colour blended behind i plus T_final bg.  The
-// gradients of one Gaussian are summed over the thread's pixels, then across
-// the warp with shuffles, before one atomic add per warp and value.
+// gradients of one Gaussian are summed over the thread's pixels, then over
+// the warp by a reduce-scatter (16 shuffles for 10 values), and each lane
+// pair adds one value with one atomic.
+#include <mutex>
+#include <unordered_map>
+
 #include "kernels.h"
 
 namespace mvgs {
@@ -32,10 +38,10 @@ struct PixelGeom {
     const DevCam* cam;
 };
 
-__device__ __forceinline__ PixelGeom pixel_geom(const BlendArgs& a, int v) {
+__device__ __forceinline__ PixelGeom pixel_geom(const BlendArgs& a, long long gt, int v) {
     PixelGeom g;
     g.cam = &a.cams[v];
-    const long long local = (long long)blockIdx.x - g.cam->tile_base;
+    const long long local = gt - g.cam->tile_base;
     const int tx = (int)(local % g.cam->tiles_x), ty = (int)(local / g.cam->tiles_x);
     g.rows = blockDim.x / a.tw;
     g.px = tx * a.tw + (int)(threadIdx.x % a.tw);
@@ -43,98 +49,124 @@ __device__ __forceinline__ PixelGeom pixel_geom(const BlendArgs& a, int v) {
     return g;
 }
 
+// Next tile of the queue for the whole block (-1 when the queue is empty).
+__device__ __forceinline__ long long next_tile(const BlendArgs& a, int* counter, int* s_slot, int* s_v) {
+    __syncthreads();  // every thread is done with the previous tile's shared values
+    if (threadIdx.x == 0) {
+        const int it = atomicAdd(counter, 1);
+        *s_slot = it;
+        if (it < a.tiles) *s_v = find_view(a.cams, a.V, a.order[it]);
+    }
+    __syncthreads();
+    const int it = *s_slot;
+    const long long gt = it < a.tiles ? (long long)a.order[it] : -1;
+    return gt;
+}
+
 template <int PPT>
-__global__ void __launch_bounds__(128) blend_forward_kernel(BlendArgs a, float* __restrict__ img,
-                                                           float* __restrict__ final_T,
+__global__ void __launch_bounds__(128) blend_forward_kernel(BlendArgs a, int* __restrict__ counter,
+                                                           float* __restrict__ img, float* __restrict__ final_T,
                                                            uint32_t* __restrict__ n_contrib) {
     __shared__ float2 s_xy[BATCH];
     __shared__ float4 s_co[BATCH];
     __shared__ float4 s_rgb[BATCH];
-    __shared__ int s_v;
+    __shared__ int s_slot, s_v;
     const int NT = blockDim.x;
-    const long long gt = blockIdx.x;
-    if (threadIdx.x == 0) s_v = find_view(a.cams, a.V, gt);
-    __syncthreads();
-    const PixelGeom pg = pixel_geom(a, s_v);
-    const DevCam& cam = *pg.cam;
-    const float fx = pg.px + 0.5f;
-    float fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
-    uint32_t last[PPT];
     constexpr uint32_t ALL = (1u << PPT) - 1u;
-    uint32_t done = 0;
+    for (;;) {
+        const long long gt = next_tile(a, counter, &s_slot, &s_v);
+        if (gt < 0) break;
+        const PixelGeom pg = pixel_geom(a, gt, s_v);
+        const DevCam& cam = *pg.cam;
+        const float fx = pg.px + 0.5f;
+        float fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
+        uint32_t last[PPT];
+        uint32_t done = 0;
 #pragma unroll
-    for (int k = 0; k < PPT; k++) {
-        const int py = pg.py0 + k * pg.rows;
-        fy[k] = py + 0.5f;
-        T[k] = 1.f;
-        C0[k] = C1[k] = C2[k] = 0.f;
-        last[k] = 0;
-        if (!(pg.px < cam.W && py < cam.H)) done |= 1u << k;
-    }
-    const long long start = a.ranges[2 * gt], end = a.ranges[2 * gt + 1];
-    for (long long b = start; b < end; b += BATCH) {
-        if (__syncthreads_count(done == ALL) == NT) break;
-        for (int i = threadIdx.x; i < BATCH; i += NT) {
-            const long long idx = b + i;
-            if (idx < end) {
-                const uint32_t r = a.sorted[idx];
-                s_xy[i] = a.xy[r];
-                s_co[i] = a.conic_o[r];
-                s_rgb[i] = a.rgb_r[r];
-            }
+        for (int k = 0; k < PPT; k++) {
+            const int py = pg.py0 + k * pg.rows;
+            fy[k] = py + 0.5f;
+            T[k] = 1.f;
+            C0[k] = C1[k] = C2[k] = 0.f;
+            last[k] = 0;
+            if (!(pg.px < cam.W && py < cam.H)) done |= 1u << k;
         }
-        __syncthreads();
-        const int cnt = (int)(end - b < (long long)BATCH ? end - b : (long long)BATCH);
-        const uint32_t base = (uint32_t)(b - start);
-        for (int j = 0; done != ALL && j < cnt; j++) {
-            const float2 m = s_xy[j];
-            const float4 cr = s_rgb[j];
-            const float dx = fx - m.x;
-            if (fabsf(dx) > cr.w) continue;  // outside the support for the whole column
-            const float4 co = s_co[j];
-#pragma unroll
-            for (int k = 0; k < PPT; k++) {
-                if ((done >> k) & 1u) continue;
-                float alpha, G;
-                if (!pair_alpha(dx, fy[k] - m.y, co, cr.w, alpha, G)) continue;
-                const float Tn = T[k] * (1.f - alpha);
-                if (Tn < kTMin) {
-                    done |= 1u << k;
-                    continue;
+        const long long start = a.ranges[2 * gt], end = a.ranges[2 * gt + 1];
+        for (long long b = start; b < end; b += BATCH) {
+            if (__syncthreads_count(done == ALL) == NT) break;
+            for (int i = threadIdx.x; i < BATCH; i += NT) {
+                const long long idx = b + i;
+                if (idx < end) {
+                    const uint32_t r = a.sorted[idx];
+                    s_xy[i] = a.xy[r];
+                    s_co[i] = a.conic_o[r];
+                    s_rgb[i] = a.rgb_r[r];
                 }
-                const float w = alpha * T[k];
-                C0[k] += cr.x * w;
-                C1[k] += cr.y * w;
-                C2[k] += cr.z * w;
-                T[k] = Tn;
-                last[k] = base + j + 1;
+            }
+            __syncthreads();
+            const int cnt = (int)(end - b < (long long)BATCH ? end - b : (long long)BATCH);
+            const uint32_t base = (uint32_t)(b - start);
+            for (int j = 0; j < cnt; j++) {
+                const float2 m = s_xy[j];
+                const float4 cr = s_rgb[j];
+                const float dx = fx - m.x;
+                if (fabsf(dx) > cr.w) continue;  // outside the support for the whole column
+                const float4 co = s_co[j];
+#pragma unroll
+                for (int k = 0; k < PPT; k++) {
+                    float alpha, G;
+                    const bool ok = pair_eval(dx, fy[k] - m.y, co, cr.w, alpha, G) && !((done >> k) & 1u);
+                    const float Tn = T[k] * (1.f - alpha);
+                    const bool stop = ok && Tn < kTMin;
+                    const bool use = ok && !stop;
+                    done |= (stop ? 1u : 0u) << k;
+                    const float w = use ? alpha * T[k] : 0.f;
+                    C0[k] += cr.x * w;
+                    C1[k] += cr.y * w;
+                    C2[k] += cr.z * w;
+                    T[k] = use ? Tn : T[k];
+                    last[k] = use ? base + j + 1 : last[k];
+                }
+                if (done == ALL) break;
             }
         }
-    }
-    const long long HW = (long long)cam.W * cam.H;
-    float* out = img + 3 * cam.pix_base;
+        const long long HW = (long long)cam.W * cam.H;
+        float* out = img + 3 * cam.pix_base;
 #pragma unroll
-    for (int k = 0; k < PPT; k++) {
-        const int py = pg.py0 + k * pg.rows;
-        if (pg.px < cam.W && py < cam.H) {
-            const long long p = (long long)py * cam.W + pg.px;
-            out[p] = C0[k] + T[k] * a.bg[0];
-            out[HW + p] = C1[k] + T[k] * a.bg[1];
-            out[2 * HW + p] = C2[k] + T[k] * a.bg[2];
-            final_T[cam.pix_base + p] = T[k];
-            n_contrib[cam.pix_base + p] = last[k];
+        for (int k = 0; k < PPT; k++) {
+            const int py = pg.py0 + k * pg.rows;
+            if (pg.px < cam.W && py < cam.H) {
+                const long long p = (long long)py * cam.W + pg.px;
+                out[p] = C0[k] + T[k] * a.bg[0];
+                out[HW + p] = C1[k] + T[k] * a.bg[1];
+                out[2 * HW + p] = C2[k] + T[k] * a.bg[2];
+                final_T[cam.pix_base + p] = T[k];
+                n_contrib[cam.pix_base + p] = last[k];
+            }
         }
     }
 }
 
-__device__ __forceinline__ float warp_sum(float x) {
+// Sum over the warp of 16 values per lane, scattered: afterwards lane l holds
+// the full sum of value 8 b4 + 4 b3 + 2 b2 + b1 (b_i the bits of l), in both
+// lanes of each pair (l, l ^ 1).
+__device__ __forceinline__ float warp_reduce_scatter16(float (&g)[16], int lane) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-    return x;
+    for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; i++) {
+            const float send = up ? g[i] : g[i + h];
+            const float keep = up ? g[i + h] : g[i];
+            g[i] = keep + __shfl_xor_sync(kFull, send, o);
+        }
+    }
+    return g[0] + __shfl_xor_sync(kFull, g[0], 1);
 }
 
 template <int PPT>
-__global__ void __launch_bounds__(128) blend_backward_kernel(BlendArgs a, const float* __restrict__ dimg,
+__global__ void __launch_bounds__(128) blend_backward_kernel(BlendArgs a, int* __restrict__ counter,
+                                                            const float* __restrict__ dimg,
                                                             const float* __restrict__ final_T,
                                                             const uint32_t* __restrict__ n_contrib,
                                                             float* __restrict__ rec_grad) {
@@ -142,94 +174,97 @@ __global__ void __launch_bounds__(128) blend_backward_kernel(BlendArgs a, const 
     __shared__ float4 s_co[BATCH];
     __shared__ float4 s_rgb[BATCH];
     __shared__ uint32_t s_rid[BATCH];
-    __shared__ int s_v;
+    __shared__ int s_slot, s_v;
     __shared__ uint32_t s_max;
     const int NT = blockDim.x;
-    const long long gt = blockIdx.x;
-    if (threadIdx.x == 0) {
-        s_v = find_view(a.cams, a.V, gt);
-        s_max = 0;
-    }
-    __syncthreads();
-    const PixelGeom pg = pixel_geom(a, s_v);
-    const DevCam& cam = *pg.cam;
-    const float fx = pg.px + 0.5f;
-    const long long HW = (long long)cam.W * cam.H;
-    const float* din = dimg + 3 * cam.pix_base;
-    float fy[PPT], T[PPT], d0[PPT], d1[PPT], d2[PPT], S0[PPT], S1[PPT], S2[PPT];
-    uint32_t last[PPT];
-    uint32_t mylast = 0;
-#pragma unroll
-    for (int k = 0; k < PPT; k++) {
-        const int py = pg.py0 + k * pg.rows;
-        fy[k] = py + 0.5f;
-        T[k] = 1.f;
-        d0[k] = d1[k] = d2[k] = 0.f;
-        last[k] = 0;
-        if (pg.px < cam.W && py < cam.H) {
-            const long long p = (long long)py * cam.W + pg.px;
-            d0[k] = din[p];
-            d1[k] = din[HW + p];
-            d2[k] = din[2 * HW + p];
-            T[k] = final_T[cam.pix_base + p];
-            last[k] = n_contrib[cam.pix_base + p];
-        }
-        // colour blended behind the current Gaussian, starting with the background
-        S0[k] = T[k] * a.bg[0];
-        S1[k] = T[k] * a.bg[1];
-        S2[k] = T[k] * a.bg[2];
-        mylast = last[k] > mylast ? last[k] : mylast;
-    }
-    atomicMax(&s_max, mylast);
-    __syncthreads();
-    const uint32_t maxlast = s_max;
-    const long long start = a.ranges[2 * gt];
     const int lane = threadIdx.x & 31;
-    for (uint32_t b = 0; b < maxlast; b += BATCH) {
+    // value this lane adds after the reduce-scatter (lane pairs share one)
+    const int my_val = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+    const bool adder = (lane & 1) == 0 && my_val < 10;
+    for (;;) {
+        const long long gt = next_tile(a, counter, &s_slot, &s_v);
+        if (gt < 0) break;
+        if (threadIdx.x == 0) s_max = 0;
         __syncthreads();
-        for (int i = threadIdx.x; i < BATCH; i += NT) {
-            const long long pos = (long long)maxlast - 1 - b - i;  // list position of slot i
-            if (pos >= 0) {
-                const uint32_t r = a.sorted[start + pos];
-                s_rid[i] = r;
-                s_xy[i] = a.xy[r];
-                s_co[i] = a.conic_o[r];
-                s_rgb[i] = a.rgb_r[r];
+        const PixelGeom pg = pixel_geom(a, gt, s_v);
+        const DevCam& cam = *pg.cam;
+        const float fx = pg.px + 0.5f;
+        const long long HW = (long long)cam.W * cam.H;
+        const float* din = dimg + 3 * cam.pix_base;
+        float fy[PPT], T[PPT], d0[PPT], d1[PPT], d2[PPT], S0[PPT], S1[PPT], S2[PPT];
+        uint32_t last[PPT];
+        uint32_t mylast = 0;
+#pragma unroll
+        for (int k = 0; k < PPT; k++) {
+            const int py = pg.py0 + k * pg.rows;
+            fy[k] = py + 0.5f;
+            T[k] = 1.f;
+            d0[k] = d1[k] = d2[k] = 0.f;
+            last[k] = 0;
+            if (pg.px < cam.W && py < cam.H) {
+                const long long p = (long long)py * cam.W + pg.px;
+                d0[k] = din[p];
+                d1[k] = din[HW + p];
+                d2[k] = din[2 * HW + p];
+                T[k] = final_T[cam.pix_base + p];
+                last[k] = n_contrib[cam.pix_base + p];
             }
+            // colour blended behind the current Gaussian, starting with the background
+            S0[k] = T[k] * a.bg[0];
+            S1[k] = T[k] * a.bg[1];
+            S2[k] = T[k] * a.bg[2];
+            mylast = last[k] > mylast ? last[k] : mylast;
         }
+        atomicMax(&s_max, mylast);
         __syncthreads();
-        const int cnt = (int)(maxlast - b < (uint32_t)BATCH ? maxlast - b : (uint32_t)BATCH);
-        for (int j = 0; j < cnt; j++) {
-            const uint32_t pos = maxlast - 1 - b - j;
-            float g[10];
+        const uint32_t maxlast = s_max;
+        const long long start = a.ranges[2 * gt];
+        for (uint32_t b = 0; b < maxlast; b += BATCH) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < BATCH; i += NT) {
+                const long long pos = (long long)maxlast - 1 - b - i;  // list position of slot i
+                if (pos >= 0) {
+                    const uint32_t r = a.sorted[start + pos];
+                    s_rid[i] = r;
+                    s_xy[i] = a.xy[r];
+                    s_co[i] = a.conic_o[r];
+                    s_rgb[i] = a.rgb_r[r];
+                }
+            }
+            __syncthreads();
+            const int cnt = (int)(maxlast - b < (uint32_t)BATCH ? maxlast - b : (uint32_t)BATCH);
+            for (int j = 0; j < cnt; j++) {
+                const uint32_t pos = maxlast - 1 - b - j;
+                float g[16];
 #pragma unroll
-            for (int i = 0; i < 10; i++) g[i] = 0.f;
-            bool any = false;
-            const float2 m = s_xy[j];
-            const float4 cr = s_rgb[j];
-            const float dx = fx - m.x;
-            if (pos < mylast && fabsf(dx) <= cr.w) {
-                const float4 co = s_co[j];
+                for (int i = 0; i < 16; i++) g[i] = 0.f;
+                bool any = false;
+                const float2 m = s_xy[j];
+                const float4 cr = s_rgb[j];
+                const float dx = fx - m.x;
+                if (pos < mylast && fabsf(dx) <= cr.w) {
+                    const float4 co = s_co[j];
 #pragma unroll
-                for (int k = 0; k < PPT; k++) {
-                    if (pos >= last[k]) continue;
-                    const float dy = fy[k] - m.y;
-                    float alpha, G;
-                    if (!pair_alpha(dx, dy, co, cr.w, alpha, G)) continue;
-                    any = true;
-                    const float om = 1.f - alpha;
-                    T[k] = T[k] / om;  // transmittance in front of this Gaussian
-                    const float w = alpha * T[k];
-                    g[6] += d0[k] * w;
-                    g[7] += d1[k] * w;
-                    g[8] += d2[k] * w;
-                    const float dLda = d0[k] * (cr.x * T[k] - S0[k] / om) + d1[k] * (cr.y * T[k] - S1[k] / om) +
-                                       d2[k] * (cr.z * T[k] - S2[k] / om);
-                    S0[k] += cr.x * w;
-                    S1[k] += cr.y * w;
-                    S2[k] += cr.z * w;
-                    if (co.w * G < kAlphaMax) {  // below the clamp alpha = o G
-                        const float dLdp = dLda * alpha;  // dL/d power = dL/dalpha o G
+                    for (int k = 0; k < PPT; k++) {
+                        const float dy = fy[k] - m.y;
+                        float alpha, G;
+                        const bool ok = pair_eval(dx, dy, co, cr.w, alpha, G) && pos < last[k];
+                        any |= ok;
+                        const float inv = __frcp_rn(1.f - alpha);
+                        const float Tk = ok ? T[k] * inv : T[k];  // transmittance in front of this Gaussian
+                        T[k] = Tk;
+                        const float w = ok ? alpha * Tk : 0.f;
+                        g[6] += d0[k] * w;
+                        g[7] += d1[k] * w;
+                        g[8] += d2[k] * w;
+                        const float dLda = d0[k] * (cr.x * Tk - S0[k] * inv) + d1[k] * (cr.y * Tk - S1[k] * inv) +
+                                           d2[k] * (cr.z * Tk - S2[k] * inv);
+                        S0[k] += cr.x * w;
+                        S1[k] += cr.y * w;
+                        S2[k] += cr.z * w;
+                        // below the clamp alpha = o G and dL/d power = dL/dalpha o G
+                        const bool live = ok && co.w * G < kAlphaMax;
+                        const float dLdp = live ? dLda * alpha : 0.f;
                         const float gx = dLdp * (co.x * dx + co.y * dy);
                         const float gy = dLdp * (co.z * dy + co.y * dx);
                         g[0] += gx;
@@ -237,19 +272,14 @@ __global__ void __launch_bounds__(128) blend_backward_kernel(BlendArgs a, const 
                         g[2] += -0.5f * dLdp * dx * dx;
                         g[3] += -dLdp * dx * dy;
                         g[4] += -0.5f * dLdp * dy * dy;
-                        g[5] += dLda * G;
+                        g[5] += live ? dLda * G : 0.f;
                         g[9] += sqrtf(gx * gx + gy * gy);
                     }
                 }
+                if (__ballot_sync(kFull, any) == 0u) continue;
+                const float sum = warp_reduce_scatter16(g, lane);
+                if (adder) atomicAdd(rec_grad + (size_t)kGradStride * s_rid[j] + my_val, sum);
             }
-            if (__ballot_sync(kFull, any) == 0u) continue;
-#pragma unroll
-            for (int i = 0; i < 10; i++) g[i] = warp_sum(g[i]);
-            // lanes 0..9 each add one value of the warp's sum
-            float mine = 0.f;
-#pragma unroll
-            for (int i = 0; i < 10; i++) mine = lane == i ? g[i] : mine;
-            if (lane < 10) atomicAdd(rec_grad + (size_t)kGradStride * s_rid[j] + lane, mine);
         }
     }
 }
@@ -263,24 +293,58 @@ void blend_shape(int tw, int th, int& threads, int& ppt) {
     threads = pix / ppt;
 }
 
+// Resident blocks over the whole GPU for a kernel at a block size (cached).
+int persistent_blocks(const void* kernel, int threads) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = static_cast<const void*>(static_cast<const char*>(kernel) + threads);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+    const int n = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    cache[key] = n;
+    return n;
+}
+
+template <class K>
+unsigned grid_for(K kernel, int threads, long long tiles) {
+    const long long n = persistent_blocks(reinterpret_cast<const void*>(kernel), threads);
+    return (unsigned)(tiles < n ? tiles : n);
+}
+
 }  // namespace
 
-void launch_blend_forward(const BlendArgs& a, float* img, float* final_T, uint32_t* n_contrib, cudaStream_t s) {
+void launch_blend_forward(const BlendArgs& a, int* counter, float* img, float* final_T, uint32_t* n_contrib,
+                          cudaStream_t s) {
     if (a.tiles == 0) return;
     int threads, ppt;
     blend_shape(a.tw, a.th, threads, ppt);
-    if (ppt == 4) blend_forward_kernel<4><<<(unsigned)a.tiles, threads, 0, s>>>(a, img, final_T, n_contrib);
-    else blend_forward_kernel<2><<<(unsigned)a.tiles, threads, 0, s>>>(a, img, final_T, n_contrib);
+    cudaMemsetAsync(counter, 0, sizeof(int), s);
+    if (ppt == 4)
+        blend_forward_kernel<4><<<grid_for(blend_forward_kernel<4>, threads, a.tiles), threads, 0, s>>>(
+            a, counter, img, final_T, n_contrib);
+    else
+        blend_forward_kernel<2><<<grid_for(blend_forward_kernel<2>, threads, a.tiles), threads, 0, s>>>(
+            a, counter, img, final_T, n_contrib);
     note_launches(1);
 }
 
-void launch_blend_backward(const BlendArgs& a, const float* dimg, const float* final_T, const uint32_t* n_contrib,
-                           float* rec_grad, cudaStream_t s) {
+void launch_blend_backward(const BlendArgs& a, int* counter, const float* dimg, const float* final_T,
+                           const uint32_t* n_contrib, float* rec_grad, cudaStream_t s) {
     if (a.tiles == 0) return;
     int threads, ppt;
     blend_shape(a.tw, a.th, threads, ppt);
-    if (ppt == 4) blend_backward_kernel<4><<<(unsigned)a.tiles, threads, 0, s>>>(a, dimg, final_T, n_contrib, rec_grad);
-    else blend_backward_kernel<2><<<(unsigned)a.tiles, threads, 0, s>>>(a, dimg, final_T, n_contrib, rec_grad);
+    cudaMemsetAsync(counter, 0, sizeof(int), s);
+    if (ppt == 4)
+        blend_backward_kernel<4><<<grid_for(blend_backward_kernel<4>, threads, a.tiles), threads, 0, s>>>(
+            a, counter, dimg, final_T, n_contrib, rec_grad);
+    else
+        blend_backward_kernel<2><<<grid_for(blend_backward_kernel<2>, threads, a.tiles), threads, 0, s>>>(
+            a, counter, dimg, final_T, n_contrib, rec_grad);
     note_launches(1);
 }
 

@@ -56,17 +56,16 @@ __device__ __forceinline__ int find_view(const DevCam* cams, int V, long long gt
 }
 
 // The blend decision and opacity of one (pixel, Gaussian) pair (Eq. 1 with
-// the 3DGS clamp and skip rules).  Returns false when the Gaussian does not
-// take part at this pixel; otherwise alpha and the Gaussian falloff G.  The
-// forward and the backward call this same function so both take the same
-// branch for every pair.
-__device__ __forceinline__ bool pair_alpha(float dx, float dy, float4 co, float radius, float& alpha, float& G) {
-    if (fabsf(dx) > radius || fabsf(dy) > radius) return false;
+// the 3DGS clamp and skip rules and the per-pixel support rule).  Everything
+// is evaluated unconditionally so callers can stay branch-free; the return
+// value says whether the Gaussian takes part at this pixel, alpha and the
+// Gaussian falloff G are valid when it does.  The forward and the backward
+// call this same function, so both take the same decision for every pair.
+__device__ __forceinline__ bool pair_eval(float dx, float dy, float4 co, float radius, float& alpha, float& G) {
     const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
-    if (power > 0.f) return false;
     G = __expf(power);
     alpha = fminf(kAlphaMax, co.w * G);
-    return alpha >= kAlphaMin;
+    return fabsf(dx) <= radius && fabsf(dy) <= radius && power <= 0.f && alpha >= kAlphaMin;
 }
 
 }  // namespace mvgs

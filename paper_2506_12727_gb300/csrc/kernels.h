@@ -79,6 +79,10 @@ void tile_sort(const uint32_t* order, const unsigned long long* tile_off, uint64
                const int* rec_v, const DevCam* cams, long long tiles, int bits, uint32_t* keys_a, uint32_t* vals_a,
                uint32_t* keys_b, uint32_t* vals_b, uint32_t* vals_out, void* tmp, cudaStream_t s);
 
+// Tiles ordered by decreasing list length (the blend's processing order).
+size_t tile_order_temp_bytes(long long tiles);
+void tile_order(const long long* ranges, long long tiles, uint32_t* order, void* tmp, cudaStream_t s);
+
 // Per-tile [start, end) of the sorted list, from the records' rectangles.
 size_t tile_count_temp_bytes(const DevCam* host_cams, int V, long long tiles);
 void tile_ranges_from_rects(const short4* rect, const int* rec_v, uint64_t R, const DevCam* cams,
@@ -92,15 +96,18 @@ struct BlendArgs {
     int tw, th;
     long long tiles;
     const long long* ranges;
+    const uint32_t* order;   // tiles in processing order (longest lists first)
     const uint32_t* sorted;
     const float2* xy;
     const float4* conic_o;
     const float4* rgb_r;
     float bg[3];
 };
-void launch_blend_forward(const BlendArgs& a, float* img, float* final_T, uint32_t* n_contrib, cudaStream_t s);
-void launch_blend_backward(const BlendArgs& a, const float* dimg, const float* final_T, const uint32_t* n_contrib,
-                           float* rec_grad, cudaStream_t s);
+// Persistent launches; `counter` is one device int of scratch (reset here).
+void launch_blend_forward(const BlendArgs& a, int* counter, float* img, float* final_T, uint32_t* n_contrib,
+                          cudaStream_t s);
+void launch_blend_backward(const BlendArgs& a, int* counter, const float* dimg, const float* final_T,
+                           const uint32_t* n_contrib, float* rec_grad, cudaStream_t s);
 
 // ---- dssim.cu --------------------------------------------------------------
 size_t dssim_temp_bytes(const int* hw, int V);

@@ -285,10 +285,11 @@ __global__ void __launch_bounds__(RS_THREADS, 2) rs_downsweep(const uint32_t* __
 }
 
 // ---------------------------------------------------------------------------
-// keys generated from the depth-ordered records (duplication fused into the
-// first radix pass): key index k belongs to the record r with
-// off[r] <= k < off[r+1]; its tile is entry k - off[r] of the record's
-// rectangle in row-major order.
+// duplication: one (tile, record) entry per tile a record's rectangle covers,
+// in the order of the depth-sorted records (rectangle tiles row-major).  Key
+// index k belongs to the record r with off[r] <= k < off[r+1].  Each block
+// emits one radix tile of entries and the histogram of their first digit, so
+// the first radix pass needs no separate histogram sweep.
 // ---------------------------------------------------------------------------
 struct DupSrc {
     const uint32_t* order;             // records by depth
@@ -300,11 +301,40 @@ struct DupSrc {
     uint32_t tiles;
 };
 
-// Finds the records covering keys [k0, k1) and stages their offsets (relative
-// to k0) in shared memory; nr < 0 when they do not fit (then keys search the
-// global offsets).
-__device__ __forceinline__ void dup_setup(const DupSrc& src, uint64_t k0, uint64_t k1, int* s_off,
-                                          unsigned long long* s_lo, int* s_n) {
+// Index of the record holding entry k: a binary search over the offsets of
+// the records that cover the block (staged in shared memory, relative to k0),
+// or over all offsets when they did not fit.
+__device__ __forceinline__ uint64_t dup_record(const DupSrc& src, const int* s_off, uint64_t rlo, int nr, uint64_t k0,
+                                               uint64_t k) {
+    if (nr > 0) {
+        const int kk = (int)(k - k0);
+        int lo = 0, hi = nr - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= kk) lo = mid; else hi = mid - 1;
+        }
+        return rlo + lo;
+    }
+    uint64_t lo = 0, hi = src.R - 1;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi + 1) >> 1;
+        if (src.off[mid] <= k) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+constexpr int DUP_ITEMS = RS_ITEMS;  // consecutive entries per thread
+
+__global__ void __launch_bounds__(RS_THREADS) dup_hist_kernel(DupSrc src, uint64_t K, uint32_t* __restrict__ keys,
+                                                             uint32_t* __restrict__ vals,
+                                                             uint32_t* __restrict__ counts, uint32_t nblocks) {
+    __shared__ uint32_t hist[RS_WARPS * 256];
+    __shared__ int s_off[RS_TILE + 1];
+    __shared__ unsigned long long s_lo;
+    __shared__ int s_n;
+    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) hist[i] = 0;
+    const uint64_t k0 = (uint64_t)blockIdx.x * RS_TILE;
+    const uint64_t k1 = K < k0 + RS_TILE ? K : k0 + RS_TILE;
     if (threadIdx.x == 0) {
         uint64_t lo = 0, hi = src.R - 1;
         while (lo < hi) {
@@ -317,116 +347,77 @@ __device__ __forceinline__ void dup_setup(const DupSrc& src, uint64_t k0, uint64
             const uint64_t mid = (lo2 + hi + 1) >> 1;
             if (src.off[mid] <= k1 - 1) lo2 = mid; else hi = mid - 1;
         }
-        *s_lo = lo;
-        *s_n = lo2 - lo + 1 <= (uint64_t)RS_TILE ? (int)(lo2 - lo + 1) : -1;
+        s_lo = lo;
+        // a record without tiles shares its offset with the next, so the
+        // records of a block can outnumber its entries; then search globally
+        s_n = lo2 - lo + 1 <= (uint64_t)RS_TILE ? (int)(lo2 - lo + 1) : -1;
     }
     __syncthreads();
-    const int nr = *s_n;
-    const uint64_t rlo = *s_lo;
-    for (int i = threadIdx.x; i <= nr; i += blockDim.x) s_off[i] = (int)((long long)src.off[rlo + i] - (long long)k0);
-    __syncthreads();
-}
-
-__device__ __forceinline__ uint32_t dup_key(const DupSrc& src, const int* s_off, uint64_t rlo, int nr, uint64_t k0,
-                                            uint64_t k, uint32_t& val) {
-    uint64_t r;
-    long long first;
-    if (nr > 0) {
-        const int kk = (int)(k - k0);
-        int lo = 0, hi = nr - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_off[mid] <= kk) lo = mid; else hi = mid - 1;
-        }
-        r = rlo + lo;
-        first = (long long)k0 + s_off[lo];
-    } else {
-        uint64_t lo = 0, hi = src.R - 1;
-        while (lo < hi) {
-            const uint64_t mid = (lo + hi + 1) >> 1;
-            if (src.off[mid] <= k) lo = mid; else hi = mid - 1;
-        }
-        r = lo;
-        first = (long long)src.off[lo];
-    }
-    const uint32_t rec = src.order[r];
-    const uint32_t j = (uint32_t)((long long)k - first);
-    const short4 rc = src.rect[rec];
-    const uint32_t w = (uint32_t)max(rc.z - rc.x, 1);
-    const uint32_t tx = rc.x + j % w, ty = rc.y + j / w;
-    const DevCam& cam = src.cams[src.rec_v[rec]];
-    const long long t = cam.tile_base + (long long)ty * cam.tiles_x + tx;
-    val = rec;
-    return (uint32_t)(t < (long long)src.tiles ? t : (long long)src.tiles - 1);  // in range even for a bad record
-}
-
-__global__ void __launch_bounds__(RS_THREADS) dup_upsweep(DupSrc src, uint64_t K, int shift,
-                                                         uint32_t* __restrict__ counts, uint32_t nblocks) {
-    __shared__ uint32_t hist[RS_WARPS * 256];
-    __shared__ int s_off[RS_TILE + 1];
-    __shared__ unsigned long long s_lo;
-    __shared__ int s_n;
-    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) hist[i] = 0;
-    const uint64_t k0 = (uint64_t)blockIdx.x * RS_TILE;
-    const uint64_t k1 = K < k0 + RS_TILE ? K : k0 + RS_TILE;
-    dup_setup(src, k0, k1, s_off, &s_lo, &s_n);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint64_t base = k0 + warp * RS_SEG + lane;
     const uint64_t rlo = s_lo;
     const int nr = s_n;
-#pragma unroll 4
-    for (int j = 0; j < RS_ITEMS; j++) {
-        const uint64_t idx = base + (uint64_t)j * 32;
-        if (idx < K) {
-            uint32_t val;
-            const uint32_t key = dup_key(src, s_off, rlo, nr, k0, idx, val);
-            atomicAdd(&hist[warp * 256 + ((key >> shift) & 0xffu)], 1u);
+    for (int i = threadIdx.x; i <= nr; i += RS_THREADS) s_off[i] = (int)((long long)src.off[rlo + i] - (long long)k0);
+    __syncthreads();
+    uint32_t* wh = hist + (threadIdx.x >> 5) * 256;
+    const uint64_t first = k0 + (uint64_t)threadIdx.x * DUP_ITEMS;
+    uint32_t kk[DUP_ITEMS], vv[DUP_ITEMS];
+#pragma unroll
+    for (int i = 0; i < DUP_ITEMS; i++) kk[i] = vv[i] = 0u;
+    if (first < K) {
+        uint64_t r = dup_record(src, s_off, rlo, nr, k0, first);
+        uint64_t rend = src.off[r + 1];
+        uint32_t rec = src.order[r];
+        short4 rc = src.rect[rec];
+        const DevCam* cam = &src.cams[src.rec_v[rec]];
+        int w = max(rc.z - rc.x, 1);
+        const uint32_t j = (uint32_t)(first - src.off[r]);
+        int tx = rc.x + (int)(j % (uint32_t)w), ty = rc.y + (int)(j / (uint32_t)w);
+#pragma unroll
+        for (int i = 0; i < DUP_ITEMS; i++) {
+            const uint64_t idx = first + i;
+            if (idx < K) {
+                while (idx >= rend) {  // next record (skipping any without tiles)
+                    r++;
+                    rend = src.off[r + 1];
+                    rec = src.order[r];
+                    rc = src.rect[rec];
+                    cam = &src.cams[src.rec_v[rec]];
+                    w = max(rc.z - rc.x, 1);
+                    tx = rc.x;
+                    ty = rc.y;
+                }
+                const long long t = cam->tile_base + (long long)ty * cam->tiles_x + tx;
+                const uint32_t key = (uint32_t)(t < (long long)src.tiles ? t : (long long)src.tiles - 1);
+                kk[i] = key;
+                vv[i] = rec;
+                atomicAdd(&wh[key & 0xffu], 1u);
+                if (++tx == rc.x + w) {
+                    tx = rc.x;
+                    ty++;
+                }
+            }
+        }
+        if (first + DUP_ITEMS <= K) {
+            uint4* kq = reinterpret_cast<uint4*>(keys + first);
+            uint4* vq = reinterpret_cast<uint4*>(vals + first);
+#pragma unroll
+            for (int q = 0; q < DUP_ITEMS / 4; q++) {
+                kq[q] = make_uint4(kk[4 * q], kk[4 * q + 1], kk[4 * q + 2], kk[4 * q + 3]);
+                vq[q] = make_uint4(vv[4 * q], vv[4 * q + 1], vv[4 * q + 2], vv[4 * q + 3]);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < DUP_ITEMS; i++)
+                if (first + i < K) {
+                    keys[first + i] = kk[i];
+                    vals[first + i] = vv[i];
+                }
         }
     }
     __syncthreads();
     uint32_t sum = 0;
 #pragma unroll
-    for (int w = 0; w < RS_WARPS; w++) sum += hist[w * 256 + threadIdx.x];
+    for (int w2 = 0; w2 < RS_WARPS; w2++) sum += hist[w2 * 256 + threadIdx.x];
     counts[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = sum;
-}
-
-template <bool WRITE_KEYS>
-__global__ void __launch_bounds__(RS_THREADS, 2) dup_downsweep(DupSrc src, uint64_t K, int shift,
-                                                              const uint32_t* __restrict__ offsets, uint32_t nblocks,
-                                                              uint32_t* __restrict__ kout,
-                                                              uint32_t* __restrict__ vout) {
-    __shared__ RankSmem sm;
-    __shared__ unsigned long long s_lo;
-    __shared__ int s_n;
-    const uint64_t k0 = (uint64_t)blockIdx.x * RS_TILE;
-    const uint64_t k1 = K < k0 + RS_TILE ? K : k0 + RS_TILE;
-    // until the scatter, the sorted staging holds the records' offsets (keys
-    // half, one entry spilling into the values half) and the generated values
-    // in block-local index order (values half, from entry 1)
-    int* s_off = reinterpret_cast<int*>(sm.skeys);
-    uint32_t* s_gval = sm.svals + 1;
-    static_assert(offsetof(RankSmem, svals) == offsetof(RankSmem, skeys) + RS_TILE * sizeof(uint32_t),
-                  "the offsets may run one entry into the values half");
-    static_assert(sizeof(sm.svals) >= (RS_TILE + 1) * sizeof(uint32_t), "values after the spilled offset fit");
-    dup_setup(src, k0, k1, s_off, &s_lo, &s_n);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int local0 = warp * RS_SEG + lane;
-    const uint64_t rlo = s_lo;
-    const int nr = s_n;
-    uint32_t k[RS_ITEMS];
-#pragma unroll
-    for (int j = 0; j < RS_ITEMS; j++) {
-        const uint64_t idx = k0 + local0 + (uint64_t)j * 32;
-        k[j] = 0u;
-        if (idx < K) {
-            uint32_t val;
-            k[j] = dup_key(src, s_off, rlo, nr, k0, idx, val);
-            s_gval[local0 + j * 32] = val;
-        }
-    }
-    // rank_and_scatter synchronises before it overwrites the staged offsets
-    rank_and_scatter<WRITE_KEYS>(sm, k, K, shift, offsets, nblocks, kout, vout,
-                                 [&](int local) { return s_gval[local]; });
 }
 
 // ---------------------------------------------------------------------------
@@ -474,6 +465,16 @@ __global__ void diff_to_counts_kernel(const DevCam* __restrict__ cams, int* __re
     const int n = cam.tiles_x * cam.tiles_y;
     for (int i = threadIdx.x; i < n; i += blockDim.x)
         counts[cam.tile_base + i] = (uint32_t)d[(i / cam.tiles_x) * W1 + (i % cam.tiles_x)];
+}
+
+// Sort key of a tile for the blend's processing order: longest lists first.
+__global__ void tile_order_keys_kernel(const long long* __restrict__ ranges, long long tiles,
+                                       uint32_t* __restrict__ keys, uint32_t* __restrict__ ids) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tiles) return;
+    const long long len = (ranges[2 * t + 1] - ranges[2 * t]) >> 2;
+    keys[t] = 0xffffu - (uint32_t)(len < 0xffff ? len : 0xffff);
+    ids[t] = (uint32_t)t;
 }
 
 __global__ void ranges_kernel(const unsigned long long* __restrict__ starts, long long tiles,
@@ -561,26 +562,18 @@ void tile_sort(const uint32_t* order, const unsigned long long* tile_off, uint64
     if (K == 0 || R == 0) return;
     const DupSrc src{order, tile_off, R, rect, rec_v, cams, (uint32_t)tiles};
     const int passes = bits > 8 ? (bits + 7) / 8 : 1;
-    // pass 0 generates the keys from the records
-    {
-        const bool last = passes == 1;
-        uint32_t* vout = last ? vals_out : vals_a;
-        radix_pass(
-            K, tmp, s,
-            [&](unsigned nb, uint32_t* counts) { dup_upsweep<<<nb, RS_THREADS, 0, s>>>(src, K, 0, counts, nb); },
-            [&](unsigned nb, uint32_t* counts) {
-                if (last) dup_downsweep<false><<<nb, RS_THREADS, 0, s>>>(src, K, 0, counts, nb, keys_a, vout);
-                else dup_downsweep<true><<<nb, RS_THREADS, 0, s>>>(src, K, 0, counts, nb, keys_a, vout);
-            });
-    }
     uint32_t *kin = keys_a, *vin = vals_a, *kout = keys_b, *vout = vals_b;
-    for (int p = 1; p < passes; p++) {
+    for (int p = 0; p < passes; p++) {
         const bool last = p == passes - 1;
         if (last) vout = vals_out;
         const int shift = 8 * p;
         radix_pass(
             K, tmp, s,
-            [&](unsigned nb, uint32_t* counts) { rs_upsweep<<<nb, RS_THREADS, 0, s>>>(kin, K, shift, counts, nb); },
+            [&](unsigned nb, uint32_t* counts) {
+                // pass 0 writes the entries and the histogram of their first digit
+                if (p == 0) dup_hist_kernel<<<nb, RS_THREADS, 0, s>>>(src, K, keys_a, vals_a, counts, nb);
+                else rs_upsweep<<<nb, RS_THREADS, 0, s>>>(kin, K, shift, counts, nb);
+            },
             [&](unsigned nb, uint32_t* counts) {
                 if (last) rs_downsweep<false><<<nb, RS_THREADS, 0, s>>>(kin, vin, kout, vout, K, shift, counts, nb);
                 else rs_downsweep<true><<<nb, RS_THREADS, 0, s>>>(kin, vin, kout, vout, K, shift, counts, nb);
@@ -592,6 +585,24 @@ void tile_sort(const uint32_t* order, const unsigned long long* tile_off, uint64
         kout = nk;
         vout = nv;
     }
+}
+
+size_t tile_order_temp_bytes(long long tiles) {
+    const size_t a = ((size_t)(tiles > 0 ? tiles : 1) * sizeof(uint32_t) + 255) / 256 * 256;
+    return 4 * a + radix_temp_bytes((uint64_t)(tiles > 0 ? tiles : 1));
+}
+
+void tile_order(const long long* ranges, long long tiles, uint32_t* order, void* tmp, cudaStream_t s) {
+    if (tiles <= 0) return;
+    const size_t a = ((size_t)tiles * sizeof(uint32_t) + 255) / 256 * 256;
+    char* base = static_cast<char*>(tmp);
+    uint32_t* ka = reinterpret_cast<uint32_t*>(base);
+    uint32_t* ia = reinterpret_cast<uint32_t*>(base + a);
+    uint32_t* kb = reinterpret_cast<uint32_t*>(base + 2 * a);
+    uint32_t* ib = reinterpret_cast<uint32_t*>(base + 3 * a);
+    tile_order_keys_kernel<<<(unsigned)ceil_div_u64((uint64_t)tiles, 256), 256, 0, s>>>(ranges, tiles, ka, ia);
+    note_launches(1);
+    radix_sort_pairs(ka, ia, kb, ib, order, (uint64_t)tiles, 16, base + 4 * a, s);
 }
 
 size_t tile_count_temp_bytes(const DevCam* host_cams, int V, long long tiles) {

@@ -49,7 +49,8 @@ class Capacity(ctypes.Structure):
 
 _LAYOUT_FIELDS = ["state_bytes", "workspace_bytes", "off_counts", "off_rec_offsets", "off_rec_gauss", "off_rec_view",
                   "off_rec_xy", "off_rec_conic_opacity", "off_rec_rgb", "off_rec_clamp", "off_rec_depth",
-                  "off_rec_rect", "off_sorted_records", "off_tile_ranges", "off_final_T", "off_n_contrib"]
+                  "off_rec_rect", "off_sorted_records", "off_tile_ranges", "off_tile_order", "off_final_T",
+                  "off_n_contrib"]
 
 
 class Layout(ctypes.Structure):
@@ -295,6 +296,7 @@ class Rasterizer:
             rect=self._view(L.off_rec_rect, R, torch.int16, 4),
             sorted=self._view(L.off_sorted_records, K, torch.int32),
             ranges=self._view(L.off_tile_ranges, int(L.tiles), torch.int64, 2),
+            tile_order=self._view(L.off_tile_order, int(L.tiles), torch.int32),
             final_T=self._view(L.off_final_T, int(L.pixels), torch.float32),
             n_contrib=self._view(L.off_n_contrib, int(L.pixels), torch.int32),
             counts=self._view(L.off_counts, 4, torch.int64))
