@@ -307,9 +307,22 @@ static proj_t project_one(const gauss_t* G, const cam_t* cam, int deg, const flo
         if (fr < m || fr > 1.0 - m) P.amb |= RA_RADIUS;
     }
     int tiles_x = ceil_div(cam->W, tw), tiles_y = ceil_div(cam->H, th);
+    /* Tiles the Gaussian covers: those that can hold a pixel centre where it
+     * passes the support rule and alpha >= 1/255.  alpha >= 1/255 needs
+     * d^T Sigma'^-1 d <= 2 ln(255 o); that ellipse's bounding box has
+     * half-widths sqrt(2 ln(255 o) Sigma'_xx), sqrt(2 ln(255 o) Sigma'_yy).
+     * The box is widened slightly (relative 1e-3 on the level, 1e-2 px) so
+     * that it also covers every pixel a float32 evaluation lets through; the
+     * image does not depend on the box, only the number of keys does. */
+    double lvl = log(255.0 * G->o);
+    if (!(lvl > 0.0)) return P;
+    double ext = 2.0 * lvl * 1.001 + 1e-3;
     double r = (double)P.radius;
-    double fx0 = floor((P.xy[0] - r) / tw), fx1 = floor((P.xy[0] + r) / tw) + 1.0;
-    double fy0 = floor((P.xy[1] - r) / th), fy1 = floor((P.xy[1] + r) / th) + 1.0;
+    double hx = sqrt(ext * P.a) + 1e-2, hy = sqrt(ext * P.c) + 1e-2;
+    hx = hx < r ? hx : r;
+    hy = hy < r ? hy : r;
+    double fx0 = floor((P.xy[0] - hx) / tw), fx1 = floor((P.xy[0] + hx) / tw) + 1.0;
+    double fy0 = floor((P.xy[1] - hy) / th), fy1 = floor((P.xy[1] + hy) / th) + 1.0;
     fx0 = fx0 < 0 ? 0 : (fx0 > tiles_x ? tiles_x : fx0);
     fx1 = fx1 < 0 ? 0 : (fx1 > tiles_x ? tiles_x : fx1);
     fy0 = fy0 < 0 ? 0 : (fy0 > tiles_y ? tiles_y : fy0);

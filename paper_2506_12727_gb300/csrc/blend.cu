@@ -9,8 +9,8 @@
 // lists first, so the heavy tiles do not form a tail.
 //
 // Each thread owns PPT pixels of one tile column (rows ly0, ly0 + R, ...), so
-// one shared-memory read of a Gaussian serves PPT pixels, and the per-pixel
-// updates are branch-free so the PPT dependency chains interleave.
+// one shared-memory read of a Gaussian serves PPT pixels; pixels that have
+// stopped, or that a Gaussian does not reach, are skipped.
 //
 // Forward per pixel (front to back): alpha = min(0.99, o G), skip alpha <
 // 1/255, stop before T (1 - alpha) < 1e-4, C += c alpha T, T *= 1 - alpha;
@@ -114,18 +114,20 @@ __global__ void __launch_bounds__(128) blend_forward_kernel(BlendArgs a, int* __
                 const float4 co = s_co[j];
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
+                    if ((done >> k) & 1u) continue;
                     float alpha, G;
-                    const bool ok = pair_eval(dx, fy[k] - m.y, co, cr.w, alpha, G) && !((done >> k) & 1u);
+                    if (!pair_eval(dx, fy[k] - m.y, co, cr.w, alpha, G)) continue;
                     const float Tn = T[k] * (1.f - alpha);
-                    const bool stop = ok && Tn < kTMin;
-                    const bool use = ok && !stop;
-                    done |= (stop ? 1u : 0u) << k;
-                    const float w = use ? alpha * T[k] : 0.f;
+                    if (Tn < kTMin) {
+                        done |= 1u << k;
+                        continue;
+                    }
+                    const float w = alpha * T[k];
                     C0[k] += cr.x * w;
                     C1[k] += cr.y * w;
                     C2[k] += cr.z * w;
-                    T[k] = use ? Tn : T[k];
-                    last[k] = use ? base + j + 1 : last[k];
+                    T[k] = Tn;
+                    last[k] = base + j + 1;
                 }
                 if (done == ALL) break;
             }
@@ -246,34 +248,34 @@ __global__ void __launch_bounds__(128) blend_backward_kernel(BlendArgs a, int* _
                     const float4 co = s_co[j];
 #pragma unroll
                     for (int k = 0; k < PPT; k++) {
+                        if (pos >= last[k]) continue;
                         const float dy = fy[k] - m.y;
                         float alpha, G;
-                        const bool ok = pair_eval(dx, dy, co, cr.w, alpha, G) && pos < last[k];
-                        any |= ok;
+                        if (!pair_eval(dx, dy, co, cr.w, alpha, G)) continue;
+                        any = true;
                         const float inv = __frcp_rn(1.f - alpha);
-                        const float Tk = ok ? T[k] * inv : T[k];  // transmittance in front of this Gaussian
-                        T[k] = Tk;
-                        const float w = ok ? alpha * Tk : 0.f;
+                        T[k] *= inv;  // transmittance in front of this Gaussian
+                        const float w = alpha * T[k];
                         g[6] += d0[k] * w;
                         g[7] += d1[k] * w;
                         g[8] += d2[k] * w;
-                        const float dLda = d0[k] * (cr.x * Tk - S0[k] * inv) + d1[k] * (cr.y * Tk - S1[k] * inv) +
-                                           d2[k] * (cr.z * Tk - S2[k] * inv);
+                        const float dLda = d0[k] * (cr.x * T[k] - S0[k] * inv) + d1[k] * (cr.y * T[k] - S1[k] * inv) +
+                                           d2[k] * (cr.z * T[k] - S2[k] * inv);
                         S0[k] += cr.x * w;
                         S1[k] += cr.y * w;
                         S2[k] += cr.z * w;
-                        // below the clamp alpha = o G and dL/d power = dL/dalpha o G
-                        const bool live = ok && co.w * G < kAlphaMax;
-                        const float dLdp = live ? dLda * alpha : 0.f;
-                        const float gx = dLdp * (co.x * dx + co.y * dy);
-                        const float gy = dLdp * (co.z * dy + co.y * dx);
-                        g[0] += gx;
-                        g[1] += gy;
-                        g[2] += -0.5f * dLdp * dx * dx;
-                        g[3] += -dLdp * dx * dy;
-                        g[4] += -0.5f * dLdp * dy * dy;
-                        g[5] += live ? dLda * G : 0.f;
-                        g[9] += sqrtf(gx * gx + gy * gy);
+                        if (co.w * G < kAlphaMax) {  // below the clamp alpha = o G
+                            const float dLdp = dLda * alpha;  // dL/d power = dL/dalpha o G
+                            const float gx = dLdp * (co.x * dx + co.y * dy);
+                            const float gy = dLdp * (co.z * dy + co.y * dx);
+                            g[0] += gx;
+                            g[1] += gy;
+                            g[2] += -0.5f * dLdp * dx * dx;
+                            g[3] += -dLdp * dx * dy;
+                            g[4] += -0.5f * dLdp * dy * dy;
+                            g[5] += dLda * G;
+                            g[9] += sqrtf(gx * gx + gy * gy);
+                        }
                     }
                 }
                 if (__ballot_sync(kFull, any) == 0u) continue;

@@ -212,13 +212,22 @@ __device__ __forceinline__ bool project(const Gauss& G, const DevCam& cam, int t
     const float lam = mid + sqrtf(fmaxf(kEigFloor, mid * mid - P.det));
     P.radius = (int)ceilf(kSigmas * sqrtf(lam));
     if (P.radius <= 0) return false;
+    // The tiles the Gaussian covers: those holding a pixel centre where it
+    // passes both the support rule (|d| <= r per axis) and alpha >= 1/255.
+    // The second needs d^T Sigma'^-1 d <= 2 ln(255 o), an ellipse whose
+    // bounding box has half-widths sqrt(2 ln(255 o) Sigma'_xx) and
+    // sqrt(2 ln(255 o) Sigma'_yy); the margins keep the box a superset of the
+    // pixels any float32 evaluation of alpha lets through.
+    const float lo = logf(255.f * G.o);
+    if (!(lo > 0.f)) return false;  // o <= 1/255: no pixel reaches 1/255
+    const float ext = 2.f * lo * 1.001f + 1e-3f;
     const float r = (float)P.radius;
-    // tiles whose pixels can lie within the radius (floor on both ends keeps
-    // at least half a pixel of slack, see the support rule in the blend)
-    const float x0 = fminf(fmaxf(floorf((P.xy.x - r) / tw), 0.f), (float)cam.tiles_x);
-    const float x1 = fminf(fmaxf(floorf((P.xy.x + r) / tw) + 1.f, 0.f), (float)cam.tiles_x);
-    const float y0 = fminf(fmaxf(floorf((P.xy.y - r) / th), 0.f), (float)cam.tiles_y);
-    const float y1 = fminf(fmaxf(floorf((P.xy.y + r) / th) + 1.f, 0.f), (float)cam.tiles_y);
+    const float hx = fminf(r, sqrtf(ext * P.a) + 1e-2f), hy = fminf(r, sqrtf(ext * P.c) + 1e-2f);
+    // floor on both ends keeps at least half a pixel of slack
+    const float x0 = fminf(fmaxf(floorf((P.xy.x - hx) / tw), 0.f), (float)cam.tiles_x);
+    const float x1 = fminf(fmaxf(floorf((P.xy.x + hx) / tw) + 1.f, 0.f), (float)cam.tiles_x);
+    const float y0 = fminf(fmaxf(floorf((P.xy.y - hy) / th), 0.f), (float)cam.tiles_y);
+    const float y1 = fminf(fmaxf(floorf((P.xy.y + hy) / th) + 1.f, 0.f), (float)cam.tiles_y);
     P.rect = make_short4((short)x0, (short)y0, (short)x1, (short)y1);
     return x0 < x1 && y0 < y1;
 }
@@ -237,7 +246,7 @@ __global__ void __launch_bounds__(256) count_visible_kernel(SceneArgs sc, const 
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= sc.n) return;
     Gauss G;
-    load_gauss(sc, g, G, false);
+    load_gauss(sc, g, G, true);
     int cnt = 0;
     for (int v = 0; v < V; v++) {
         Proj P;

@@ -367,3 +367,32 @@ def test_adc_invariants_and_single_pixel_equality():
     assert E1.max() > 0
     np.testing.assert_allclose(E1, E2, rtol=1e-12, atol=1e-15)
     np.testing.assert_allclose(E2, Eold, rtol=1e-12, atol=1e-15)
+
+
+def test_tile_rect_covers_every_pixel_a_gaussian_can_reach():
+    """The tile rectangle (bounding box of the alpha >= 1/255 ellipse inside
+    the support square) holds every pixel where the Gaussian passes the
+    support rule and the 1/255 test, checked pixel by pixel."""
+    sc = synth.make_scene(400, 0, seed=31)
+    sc.opacity_logits[:] = np.random.default_rng(1).normal(0, 2.5, sc.n).astype(np.float32)
+    cams = synth.make_cameras([(160, 120), (90, 70)], radius=3.0, seed=32)
+    for tile in ((8, 8), (16, 16), (32, 16)):
+        P = oracle.project(sc, cams, tile)
+        for v in range(cams.V):
+            W, H = int(cams.width[v]), int(cams.height[v])
+            ys, xs = np.mgrid[0:H, 0:W]
+            for g in range(sc.n):
+                r = v * sc.n + g
+                dx = xs + 0.5 - P["xy"][r, 0]
+                dy = ys + 0.5 - P["xy"][r, 1]
+                A, B, C = P["conic"][r]
+                power = -0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy
+                alpha = np.minimum(0.99, P["opac"][r] * np.exp(power))
+                rad = P["radius"][r]
+                hit = (np.abs(dx) <= rad) & (np.abs(dy) <= rad) & (alpha >= 1 / 255)
+                if not P["valid"][r]:
+                    assert not hit.any() or P["opac"][r] <= 1 / 255 or rad == 0
+                    continue
+                x0, y0, x1, y1 = P["rect"][r]
+                tx, ty = xs[hit] // tile[0], ys[hit] // tile[1]
+                assert np.all((tx >= x0) & (tx < x1) & (ty >= y0) & (ty < y1)), (v, g)
