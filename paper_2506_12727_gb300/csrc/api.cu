@@ -217,7 +217,8 @@ mvgs_status make_plan(long long n, const mvgs_camera* cams, int V, const mvgs_co
     P.w_keys_b = w.take(K * sizeof(uint32_t));
     P.w_vals_a = w.take(K * sizeof(uint32_t));
     P.w_vals_b = w.take(K * sizeof(uint32_t));
-    P.w_radix = w.take(radix_temp_bytes(big));
+    P.w_radix = w.take(radix_temp_bytes(big) > tile_sort_temp_bytes(K) ? radix_temp_bytes(big)
+                                                                          : tile_sort_temp_bytes(K));
     P.w_tcount = w.take(tile_count_temp_bytes(P.cams.data(), V, tiles));
     P.w_torder = w.take(tile_order_temp_bytes(tiles));
     P.w_counter = w.take(sizeof(int));

@@ -64,6 +64,7 @@ void scan_gather_u32_to_u64(const uint32_t* in, const uint32_t* idx, unsigned lo
                             cudaStream_t s);
 
 size_t radix_temp_bytes(uint64_t n);
+size_t tile_sort_temp_bytes(uint64_t K);
 // Stable LSD sort of (key, value) pairs on key bits [0, bits).  Input in
 // (keys_a, vals_a), which are overwritten; buffers _b are scratch; the sorted
 // values end in vals_out.

@@ -325,36 +325,34 @@ __device__ __forceinline__ uint64_t dup_record(const DupSrc& src, const int* s_o
 
 constexpr int DUP_ITEMS = RS_ITEMS;  // consecutive entries per thread
 
-__global__ void __launch_bounds__(RS_THREADS) dup_hist_kernel(DupSrc src, uint64_t K, uint32_t* __restrict__ keys,
+// first[b] = the record holding entry b * TILE, for every radix block b:
+// each record fills the blocks whose first entry it holds, so no block has to
+// search for its records.  first[nblocks] = R - 1.
+__global__ void block_starts_kernel(const unsigned long long* __restrict__ off, uint64_t R, uint32_t nblocks,
+                                    uint32_t* __restrict__ first) {
+    const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r == 0) first[nblocks] = (uint32_t)(R - 1);
+    if (r >= R) return;
+    const uint64_t b0 = (off[r] + RS_TILE - 1) / RS_TILE;
+    const uint64_t b1 = (off[r + 1] + RS_TILE - 1) / RS_TILE;  // exclusive
+    for (uint64_t b = b0; b < b1 && b < nblocks; b++) first[b] = (uint32_t)r;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) dup_hist_kernel(DupSrc src, const uint32_t* __restrict__ first_rec,
+                                                             uint64_t K, uint32_t* __restrict__ keys,
                                                              uint32_t* __restrict__ vals,
                                                              uint32_t* __restrict__ counts, uint32_t nblocks) {
     __shared__ uint32_t hist[RS_WARPS * 256];
-    __shared__ int s_off[RS_TILE + 1];
-    __shared__ unsigned long long s_lo;
-    __shared__ int s_n;
+    __shared__ int s_off[RS_TILE + 2];
     for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) hist[i] = 0;
     const uint64_t k0 = (uint64_t)blockIdx.x * RS_TILE;
-    const uint64_t k1 = K < k0 + RS_TILE ? K : k0 + RS_TILE;
-    if (threadIdx.x == 0) {
-        uint64_t lo = 0, hi = src.R - 1;
-        while (lo < hi) {
-            const uint64_t mid = (lo + hi + 1) >> 1;
-            if (src.off[mid] <= k0) lo = mid; else hi = mid - 1;
-        }
-        uint64_t lo2 = lo;
-        hi = src.R - 1;
-        while (lo2 < hi) {
-            const uint64_t mid = (lo2 + hi + 1) >> 1;
-            if (src.off[mid] <= k1 - 1) lo2 = mid; else hi = mid - 1;
-        }
-        s_lo = lo;
-        // a record without tiles shares its offset with the next, so the
-        // records of a block can outnumber its entries; then search globally
-        s_n = lo2 - lo + 1 <= (uint64_t)RS_TILE ? (int)(lo2 - lo + 1) : -1;
-    }
-    __syncthreads();
-    const uint64_t rlo = s_lo;
-    const int nr = s_n;
+    // records [rlo, rlo + nr) hold this block's entries (the next block's
+    // first record may start inside it); a record without tiles shares its
+    // offset with the next, so they can outnumber the entries: then search
+    // all offsets instead
+    const uint64_t rlo = first_rec[blockIdx.x];
+    const uint64_t rhi = first_rec[blockIdx.x + 1];
+    const int nr = rhi - rlo + 1 <= (uint64_t)RS_TILE ? (int)(rhi - rlo + 1) : -1;
     for (int i = threadIdx.x; i <= nr; i += RS_THREADS) s_off[i] = (int)((long long)src.off[rlo + i] - (long long)k0);
     __syncthreads();
     uint32_t* wh = hist + (threadIdx.x >> 5) * 256;
@@ -510,7 +508,11 @@ static uint64_t radix_blocks(uint64_t n) { return ceil_div_u64(n, RS_TILE); }
 size_t radix_temp_bytes(uint64_t n) {
     const uint64_t nb = radix_blocks(n > 0 ? n : 1);
     const size_t counts = ((256 * nb * sizeof(uint32_t)) + 255) / 256 * 256;
-    return counts + scan_temp_bytes(256 * nb);
+    return counts + (scan_temp_bytes(256 * nb) + 255) / 256 * 256;
+}
+
+size_t tile_sort_temp_bytes(uint64_t K) {
+    return radix_temp_bytes(K) + ((radix_blocks(K > 0 ? K : 1) + 1) * sizeof(uint32_t) + 255) / 256 * 256;
 }
 
 namespace {
@@ -560,6 +562,8 @@ void tile_sort(const uint32_t* order, const unsigned long long* tile_off, uint64
                const int* rec_v, const DevCam* cams, long long tiles, int bits, uint32_t* keys_a, uint32_t* vals_a,
                uint32_t* keys_b, uint32_t* vals_b, uint32_t* vals_out, void* tmp, cudaStream_t s) {
     if (K == 0 || R == 0) return;
+    // the radix pass uses the front of tmp; the block starts go behind it
+    uint32_t* first_rec = reinterpret_cast<uint32_t*>(static_cast<char*>(tmp) + radix_temp_bytes(K));
     const DupSrc src{order, tile_off, R, rect, rec_v, cams, (uint32_t)tiles};
     const int passes = bits > 8 ? (bits + 7) / 8 : 1;
     uint32_t *kin = keys_a, *vin = vals_a, *kout = keys_b, *vout = vals_b;
@@ -571,8 +575,13 @@ void tile_sort(const uint32_t* order, const unsigned long long* tile_off, uint64
             K, tmp, s,
             [&](unsigned nb, uint32_t* counts) {
                 // pass 0 writes the entries and the histogram of their first digit
-                if (p == 0) dup_hist_kernel<<<nb, RS_THREADS, 0, s>>>(src, K, keys_a, vals_a, counts, nb);
-                else rs_upsweep<<<nb, RS_THREADS, 0, s>>>(kin, K, shift, counts, nb);
+                if (p == 0) {
+                    block_starts_kernel<<<(unsigned)ceil_div_u64(R, 256), 256, 0, s>>>(tile_off, R, nb, first_rec);
+                    dup_hist_kernel<<<nb, RS_THREADS, 0, s>>>(src, first_rec, K, keys_a, vals_a, counts, nb);
+                    note_launches(1);
+                } else {
+                    rs_upsweep<<<nb, RS_THREADS, 0, s>>>(kin, K, shift, counts, nb);
+                }
             },
             [&](unsigned nb, uint32_t* counts) {
                 if (last) rs_downsweep<false><<<nb, RS_THREADS, 0, s>>>(kin, vin, kout, vout, K, shift, counts, nb);
