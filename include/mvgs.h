@@ -182,6 +182,20 @@ mvgs_status mvgs_dssim_loss(const float* img, const float* target, const int32_t
                             float* loss_per_view, float* dL_dimg, void* workspace, size_t workspace_bytes,
                             mvgs_stream stream);
 
+/* mvgs_dssim_loss without a caller workspace, for callers that cannot
+ * allocate device memory (a plug-in inside another framework's memory pool, a
+ * process that reserves all device memory up front, a loop that must never
+ * enter the allocator).  No counterpart in the paper.  Same arguments and
+ * results as mvgs_dssim_loss minus the workspace: the scratch is an 80 MiB
+ * static device array inside the library (every GPU that loads the library
+ * holds it until exit), enough for about 2.2 million pixels per call (one
+ * 1920x1080 view); larger calls return MVGS_ENOSPACE without launching.  The
+ * first call on a device looks up the array's address on that device (make
+ * that call before any stream capture).  Calls share the array, so calls
+ * that overlap on the GPU race; nothing in it needs clearing between calls. */
+mvgs_status mvgs_dssim_loss_noalloc(const float* img, const float* target, const int32_t* hw, int32_t V,
+                                    float lambda, float* loss_per_view, float* dL_dimg, mvgs_stream stream);
+
 /* Adds this batch's densification statistics into running per-Gaussian sums
  * (Sec. 5.2.2):
  *   accum_e1[g] += sum_views e1[record]           (E_1: norm, then add)

@@ -20,8 +20,17 @@ void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); 
 }  // namespace mvgs
 
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
+
+namespace mvgs {
+int record_error(int st, const char* msg) {
+    g_last_error = msg;
+    return st;
+}
+}  // namespace mvgs
+
+namespace {
 
 mvgs_status fail(mvgs_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
 mvgs_status fail(mvgs_status st, const char* fmt, ...) {

@@ -12,6 +12,9 @@ namespace mvgs {
 // Process-wide count of kernels launched by the library (api.cu).
 void note_launches(int k);
 
+// Sets the calling thread's last error message (api.cu) and returns `st`.
+int record_error(int st, const char* msg);
+
 // ---- preprocess.cu -------------------------------------------------------
 void upload_cams(const DevCam* host, int V, DevCam* dst, cudaStream_t s);
 

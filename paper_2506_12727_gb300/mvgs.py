@@ -61,7 +61,7 @@ class Layout(ctypes.Structure):
 # every symbol declared in include/mvgs.h
 EXPORTS = ["mvgs_render_layout", "mvgs_render_views", "mvgs_render_views_backward", "mvgs_dssim_workspace_size",
            "mvgs_dssim_loss", "mvgs_adc_accumulate", "mvgs_profile_enable", "mvgs_profile_read", "mvgs_stage_name",
-           "mvgs_launch_count", "mvgs_last_error"]
+           "mvgs_launch_count", "mvgs_dssim_loss_noalloc", "mvgs_last_error"]
 
 
 def load_library(path: str | None = None):
@@ -78,6 +78,8 @@ def load_library(path: str | None = None):
     lib.mvgs_dssim_workspace_size.restype = SZ
     lib.mvgs_dssim_loss.argtypes = [P, P, P, I32, ctypes.c_float, P, P, P, SZ, P]
     lib.mvgs_adc_accumulate.argtypes = [P, I64, P, P, P, P, P, P]
+    lib.mvgs_dssim_loss_noalloc.argtypes = [P, P, P, I32, ctypes.c_float, P, P, P]
+    lib.mvgs_dssim_loss_noalloc.restype = ctypes.c_int
     lib.mvgs_last_error.restype = ctypes.c_char_p
     lib.mvgs_profile_enable.argtypes = [I32]
     lib.mvgs_profile_enable.restype = ctypes.c_int
@@ -192,6 +194,14 @@ def dssim_loss(img, target, hw, lam, loss_per_view, dL_dimg, workspace, stream=N
     st = _lib.mvgs_dssim_loss(_ptr(img), _ptr(target), hw.ctypes.data_as(ctypes.c_void_p), hw.shape[0],
                               ctypes.c_float(lam), _ptr(loss_per_view), _ptr(dL_dimg), _ptr(workspace),
                               workspace.numel(), _stream(stream))
+    _check(st)
+
+
+def dssim_loss_noalloc(img, target, hw, lam, loss_per_view, dL_dimg, stream=None):
+    """mvgs_dssim_loss with the library's static scratch (no workspace)."""
+    hw = np.ascontiguousarray(hw, dtype=np.int32)
+    st = _lib.mvgs_dssim_loss_noalloc(_ptr(img), _ptr(target), hw.ctypes.data_as(ctypes.c_void_p), hw.shape[0],
+                                      ctypes.c_float(lam), _ptr(loss_per_view), _ptr(dL_dimg), _stream(stream))
     _check(st)
 
 
