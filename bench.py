@@ -34,6 +34,14 @@ WORKLOAD = "multiview_500k_4x1264x832"
 LAMBDA = 0.2
 METRIC = "fwd+bwd views/s (batched multi-view vs per-view loop) at oracle tol; serve p50/p99"
 FP32_LANES_PER_SM = 128
+# Algorithmic FP32 work of the blend kernels per (pixel, list entry) pair.
+# Examining a pair: offsets, the quadratic form, exp argument, opacity
+# product and clamp (14 FLOP, plus one ex2).  Blending it (forward):
+# transmittance update, weight and three colour FMAs (8 FLOP).  Its gradient
+# (backward): transmittance recovery, colour, alpha, power, mean2d, conic,
+# opacity and E1 terms (50 FLOP, counted from the chain rule of Eq. 1).
+FWD_FLOP_PER_EXAMINED, FWD_FLOP_PER_BLENDED = 14, 8
+BWD_FLOP_PER_EXAMINED, BWD_FLOP_PER_BLENDED = 14, 50
 
 
 def parse():
@@ -44,6 +52,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--ppt", type=int, default=0, help="blend pixels per thread (0 = automatic)")
     ap.add_argument("--no-loop", action="store_true", help="skip the per-view launch loop")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) measurement")
@@ -129,7 +138,7 @@ def run_ours(args, rank, world):
               ("means", "log_scales", "quats", "opacity_logits", "sh")}
     tgt = torch.tensor(synth.pack_images(targets), device=dev)
     sc = mvgs.make_scene(params, scene.sh_degree)
-    rz = mvgs.Rasterizer(cams, tile=tile)
+    rz = mvgs.Rasterizer(cams, tile=tile, pixels_per_thread=args.ppt)
     grads = {k: torch.empty_like(v) for k, v in params.items()}
     dssim_ws = torch.empty(mvgs.dssim_workspace_size(hw), dtype=torch.uint8, device=dev)
     loss = torch.empty(V, device=dev)
@@ -202,7 +211,8 @@ def run_ours(args, rank, world):
             cv = cams.subset([v])
             hv = hw[v:v + 1]
             off = synth.view_offsets(cams)
-            singles.append((mvgs.Rasterizer(cv, tile=tile), tgt[off[v]:off[v + 1]].contiguous(), hv,
+            singles.append((mvgs.Rasterizer(cv, tile=tile, pixels_per_thread=args.ppt),
+                            tgt[off[v]:off[v + 1]].contiguous(), hv,
                             torch.empty(1, device=dev), torch.empty(int(off[v + 1] - off[v]), device=dev),
                             torch.empty(mvgs.dssim_workspace_size(hv), dtype=torch.uint8, device=dev)))
 
@@ -238,6 +248,7 @@ def run_ours(args, rank, world):
         "config": {"workload": args.workload, "gaussians": n, "sh_degree": scene.sh_degree, "views": V,
                    "resolutions": sorted({f"{w}x{h}" for w, h in zip(cams.width, cams.height)}),
                    "loss": "0.8 L1 + 0.2 D-SSIM (11x11, sigma 1.5)", "adc": True, "tile": args.tile,
+                   "pixels_per_thread": args.ppt or "auto",
                    "records": needed[0], "keys": needed[1],
                    "l2": "512 MB buffer written between timed steps (L2 is 129 MB); per-step working set > 1 GB",
                    "parallelism": "replicas" if world > 1 else "single"},
@@ -288,15 +299,24 @@ def roofline(stages, args, needed, rz, clk):
                 "algorithmic": f"{passes} passes x 16 B x {K} keys"}
     if dom in ("blend_forward", "blend_backward"):
         rec = rz.records()
-        nc = rec["n_contrib"].to(torch.int64).sum().item()
-        flop_per_pair = 18.0 if dom == "blend_forward" else 60.0
-        flops = flop_per_pair * nc
+        stats = rec["pixel_stats"].to(torch.int64)
+        examined = stats[:, 0].sum().item()   # (pixel, entry) pairs the forward examined
+        blended = stats[:, 1].sum().item()    # (pixel, Gaussian) pairs blended
+        before_last = rec["n_contrib"].to(torch.int64).sum().item()  # pairs the backward examines
+        if dom == "blend_forward":
+            flops = FWD_FLOP_PER_EXAMINED * examined + FWD_FLOP_PER_BLENDED * blended
+            what = (f"{FWD_FLOP_PER_EXAMINED} FLOP x {examined} examined + {FWD_FLOP_PER_BLENDED} FLOP x {blended} "
+                    "blended (pixel, entry) pairs")
+        else:
+            flops = BWD_FLOP_PER_EXAMINED * before_last + BWD_FLOP_PER_BLENDED * blended
+            what = (f"{BWD_FLOP_PER_EXAMINED} FLOP x {before_last} examined + {BWD_FLOP_PER_BLENDED} FLOP x "
+                    f"{blended} blended (pixel, entry) pairs")
         mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1455.0)
         peak = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
         ach = flops / (ms_launch / 1e3) / 1e12
         return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": None, "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)",
-                "algorithmic": f"{flop_per_pair:.0f} FLOP x {nc} (pixel, list entry) pairs up to the last contributor"}
+                "algorithmic": what}
     # other stages: bytes moved estimate
     byte_est = {"preprocess": 236.0 * rz.n + 64.0 * R, "duplicate": 8.0 * K + 12.0 * R,
                 "depth_sort": 4 * 16.0 * R, "preprocess_backward": 236.0 * 2 * rz.n + 48.0 * R}

@@ -98,6 +98,12 @@ typedef struct mvgs_config {
     int32_t tile_w, tile_h;
     float bg[3];      /* background colour added with the final transmittance */
     uint32_t flags;   /* reserved, must be 0 */
+    int32_t pixels_per_thread;  /* blend threads each own this many pixels of a
+                                   tile column: 0 = automatic, else 1, 2, 4 or 8
+                                   with tile_w * tile_h / pixels_per_thread a
+                                   multiple of 32 and at most 256, and
+                                   pixels_per_thread dividing tile_h.  Results
+                                   do not depend on it. */
 } mvgs_config;
 
 /* Capacities the caller sized `state` and `workspace` for:
@@ -129,6 +135,8 @@ typedef struct mvgs_layout {
     size_t off_tile_order;           /* uint32[tiles]: blend processing order (longest lists first) */
     size_t off_final_T;              /* float[pixels]: transmittance after blending */
     size_t off_n_contrib;            /* uint32[pixels]: list position one past the last contributor */
+    size_t off_pixel_stats;          /* uint32x2[pixels]: list entries the pixel examined before it
+                                        stopped, and the number of Gaussians it blended */
     int64_t tiles;                   /* total tiles over all views                 */
     int64_t pixels;                  /* total pixels over all views                */
 } mvgs_layout;

@@ -139,6 +139,12 @@ mvgs_status check_config(const mvgs_config* cfg) {
     if (!side_ok || tw * th > 512)
         return fail(MVGS_EINVAL, "unsupported tile %dx%d (sides 8, 16 or 32, at most 512 pixels)", tw, th);
     if (cfg->flags != 0) return fail(MVGS_EINVAL, "flags must be 0");
+    const int ppt = cfg->pixels_per_thread;
+    if (ppt != 0) {
+        const int threads = ppt > 0 ? tw * th / ppt : 0;
+        if (!(ppt == 1 || ppt == 2 || ppt == 4 || ppt == 8) || th % ppt || threads % 32 || threads > 256)
+            return fail(MVGS_EINVAL, "pixels_per_thread %d does not fit a %dx%d tile", ppt, tw, th);
+    }
     return MVGS_OK;
 }
 
@@ -205,6 +211,7 @@ mvgs_status make_plan(long long n, const mvgs_camera* cams, int V, const mvgs_co
     L.off_tile_order = s.take((size_t)tiles * sizeof(uint32_t));
     L.off_final_T = s.take((size_t)pixels * sizeof(float));
     L.off_n_contrib = s.take((size_t)pixels * sizeof(uint32_t));
+    L.off_pixel_stats = s.take((size_t)pixels * 2 * sizeof(uint32_t));
     L.state_bytes = s.off;
     L.tiles = tiles;
     L.pixels = pixels;
@@ -451,6 +458,7 @@ mvgs_status mvgs_render_views(const mvgs_scene* scene, const mvgs_camera* cams, 
     ba.V = V;
     ba.tw = tw;
     ba.th = th;
+    ba.ppt = cfg->pixels_per_thread;
     ba.tiles = P.tiles;
     ba.ranges = ranges;
     ba.order = at<uint32_t>(state, L.off_tile_order);
@@ -462,7 +470,7 @@ mvgs_status mvgs_render_views(const mvgs_scene* scene, const mvgs_camera* cams, 
     {
         StageTimer t(MVGS_STAGE_BLEND_FORWARD, s);
         launch_blend_forward(ba, at<int>(workspace, P.w_counter), images, at<float>(state, L.off_final_T),
-                             at<uint32_t>(state, L.off_n_contrib), s);
+                             at<uint32_t>(state, L.off_n_contrib), at<uint2>(state, L.off_pixel_stats), s);
     }
     return cuda_check("render");
 }
@@ -501,6 +509,7 @@ mvgs_status mvgs_render_views_backward(const mvgs_scene* scene, const mvgs_camer
     ba.V = V;
     ba.tw = cfg->tile_w;
     ba.th = cfg->tile_h;
+    ba.ppt = cfg->pixels_per_thread;
     ba.tiles = P.tiles;
     ba.ranges = at<long long>(state, L.off_tile_ranges);
     ba.order = at<uint32_t>(state, L.off_tile_order);

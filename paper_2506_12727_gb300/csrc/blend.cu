@@ -64,9 +64,10 @@ __device__ __forceinline__ long long next_tile(const BlendArgs& a, int* counter,
 }
 
 template <int PPT>
-__global__ void __launch_bounds__(128) blend_forward_kernel(BlendArgs a, int* __restrict__ counter,
+__global__ void __launch_bounds__(PPT >= 4 ? 128 : 256) blend_forward_kernel(BlendArgs a, int* __restrict__ counter,
                                                            float* __restrict__ img, float* __restrict__ final_T,
-                                                           uint32_t* __restrict__ n_contrib) {
+                                                           uint32_t* __restrict__ n_contrib,
+                                                           uint2* __restrict__ pixel_stats) {
     __shared__ float2 s_xy[BATCH];
     __shared__ float4 s_co[BATCH];
     __shared__ float4 s_rgb[BATCH];
@@ -80,8 +81,9 @@ __global__ void __launch_bounds__(128) blend_forward_kernel(BlendArgs a, int* __
         const DevCam& cam = *pg.cam;
         const float fx = pg.px + 0.5f;
         float fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
-        uint32_t last[PPT];
+        uint32_t last[PPT], stop[PPT], nblend[PPT];
         uint32_t done = 0;
+        const long long start = a.ranges[2 * gt], end = a.ranges[2 * gt + 1];
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
             const int py = pg.py0 + k * pg.rows;
@@ -89,9 +91,10 @@ __global__ void __launch_bounds__(128) blend_forward_kernel(BlendArgs a, int* __
             T[k] = 1.f;
             C0[k] = C1[k] = C2[k] = 0.f;
             last[k] = 0;
+            stop[k] = (uint32_t)(end - start);  // list position where the pixel stopped
+            nblend[k] = 0;
             if (!(pg.px < cam.W && py < cam.H)) done |= 1u << k;
         }
-        const long long start = a.ranges[2 * gt], end = a.ranges[2 * gt + 1];
         for (long long b = start; b < end; b += BATCH) {
             if (__syncthreads_count(done == ALL) == NT) break;
             for (int i = threadIdx.x; i < BATCH; i += NT) {
@@ -120,6 +123,7 @@ __global__ void __launch_bounds__(128) blend_forward_kernel(BlendArgs a, int* __
                     const float Tn = T[k] * (1.f - alpha);
                     if (Tn < kTMin) {
                         done |= 1u << k;
+                        stop[k] = base + j + 1;
                         continue;
                     }
                     const float w = alpha * T[k];
@@ -128,6 +132,7 @@ __global__ void __launch_bounds__(128) blend_forward_kernel(BlendArgs a, int* __
                     C2[k] += cr.z * w;
                     T[k] = Tn;
                     last[k] = base + j + 1;
+                    nblend[k]++;
                 }
                 if (done == ALL) break;
             }
@@ -144,6 +149,7 @@ __global__ void __launch_bounds__(128) blend_forward_kernel(BlendArgs a, int* __
                 out[2 * HW + p] = C2[k] + T[k] * a.bg[2];
                 final_T[cam.pix_base + p] = T[k];
                 n_contrib[cam.pix_base + p] = last[k];
+                pixel_stats[cam.pix_base + p] = make_uint2(stop[k], nblend[k]);
             }
         }
     }
@@ -167,7 +173,7 @@ __device__ __forceinline__ float warp_reduce_scatter16(float (&g)[16], int lane)
 }
 
 template <int PPT>
-__global__ void __launch_bounds__(128) blend_backward_kernel(BlendArgs a, int* __restrict__ counter,
+__global__ void __launch_bounds__(PPT >= 4 ? 128 : 256) blend_backward_kernel(BlendArgs a, int* __restrict__ counter,
                                                             const float* __restrict__ dimg,
                                                             const float* __restrict__ final_T,
                                                             const uint32_t* __restrict__ n_contrib,
@@ -288,10 +294,11 @@ __global__ void __launch_bounds__(128) blend_backward_kernel(BlendArgs a, int* _
 
 // threads per block and pixels per thread for a tile size (tile sides 8, 16
 // or 32 with at most 512 pixels: the thread count is a multiple of 32 and
-// divides evenly into tile rows)
-void blend_shape(int tw, int th, int& threads, int& ppt) {
+// divides evenly into tile rows); a requested pixels-per-thread was checked
+// by the caller
+void blend_shape(int tw, int th, int req, int& threads, int& ppt) {
     const int pix = tw * th;
-    ppt = pix >= 128 ? 4 : 2;
+    ppt = req > 0 ? req : (pix >= 128 ? 4 : 2);
     threads = pix / ppt;
 }
 
@@ -321,17 +328,21 @@ unsigned grid_for(K kernel, int threads, long long tiles) {
 }  // namespace
 
 void launch_blend_forward(const BlendArgs& a, int* counter, float* img, float* final_T, uint32_t* n_contrib,
-                          cudaStream_t s) {
+                          uint2* pixel_stats, cudaStream_t s) {
     if (a.tiles == 0) return;
     int threads, ppt;
-    blend_shape(a.tw, a.th, threads, ppt);
+    blend_shape(a.tw, a.th, a.ppt, threads, ppt);
     cudaMemsetAsync(counter, 0, sizeof(int), s);
-    if (ppt == 4)
-        blend_forward_kernel<4><<<grid_for(blend_forward_kernel<4>, threads, a.tiles), threads, 0, s>>>(
-            a, counter, img, final_T, n_contrib);
-    else
-        blend_forward_kernel<2><<<grid_for(blend_forward_kernel<2>, threads, a.tiles), threads, 0, s>>>(
-            a, counter, img, final_T, n_contrib);
+#define MVGS_BF(P)                                                                                               \
+    blend_forward_kernel<P><<<grid_for(blend_forward_kernel<P>, threads, a.tiles), threads, 0, s>>>(            \
+        a, counter, img, final_T, n_contrib, pixel_stats)
+    switch (ppt) {
+        case 1: MVGS_BF(1); break;
+        case 2: MVGS_BF(2); break;
+        case 8: MVGS_BF(8); break;
+        default: MVGS_BF(4); break;
+    }
+#undef MVGS_BF
     note_launches(1);
 }
 
@@ -339,14 +350,18 @@ void launch_blend_backward(const BlendArgs& a, int* counter, const float* dimg, 
                            const uint32_t* n_contrib, float* rec_grad, cudaStream_t s) {
     if (a.tiles == 0) return;
     int threads, ppt;
-    blend_shape(a.tw, a.th, threads, ppt);
+    blend_shape(a.tw, a.th, a.ppt, threads, ppt);
     cudaMemsetAsync(counter, 0, sizeof(int), s);
-    if (ppt == 4)
-        blend_backward_kernel<4><<<grid_for(blend_backward_kernel<4>, threads, a.tiles), threads, 0, s>>>(
-            a, counter, dimg, final_T, n_contrib, rec_grad);
-    else
-        blend_backward_kernel<2><<<grid_for(blend_backward_kernel<2>, threads, a.tiles), threads, 0, s>>>(
-            a, counter, dimg, final_T, n_contrib, rec_grad);
+#define MVGS_BB(P)                                                                                               \
+    blend_backward_kernel<P><<<grid_for(blend_backward_kernel<P>, threads, a.tiles), threads, 0, s>>>(          \
+        a, counter, dimg, final_T, n_contrib, rec_grad)
+    switch (ppt) {
+        case 1: MVGS_BB(1); break;
+        case 2: MVGS_BB(2); break;
+        case 8: MVGS_BB(8); break;
+        default: MVGS_BB(4); break;
+    }
+#undef MVGS_BB
     note_launches(1);
 }
 

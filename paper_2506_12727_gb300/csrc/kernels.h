@@ -98,6 +98,7 @@ struct BlendArgs {
     const DevCam* cams;
     int V;
     int tw, th;
+    int ppt;                 // pixels per thread (0 = automatic)
     long long tiles;
     const long long* ranges;
     const uint32_t* order;   // tiles in processing order (longest lists first)
@@ -109,7 +110,7 @@ struct BlendArgs {
 };
 // Persistent launches; `counter` is one device int of scratch (reset here).
 void launch_blend_forward(const BlendArgs& a, int* counter, float* img, float* final_T, uint32_t* n_contrib,
-                          cudaStream_t s);
+                          uint2* pixel_stats, cudaStream_t s);
 void launch_blend_backward(const BlendArgs& a, int* counter, const float* dimg, const float* final_T,
                            const uint32_t* n_contrib, float* rec_grad, cudaStream_t s);
 

@@ -40,7 +40,7 @@ class Scene(ctypes.Structure):
 
 class Config(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("bg", ctypes.c_float * 3),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("pixels_per_thread", ctypes.c_int32)]
 
 
 class Capacity(ctypes.Structure):
@@ -50,7 +50,7 @@ class Capacity(ctypes.Structure):
 _LAYOUT_FIELDS = ["state_bytes", "workspace_bytes", "off_counts", "off_rec_offsets", "off_rec_gauss", "off_rec_view",
                   "off_rec_xy", "off_rec_conic_opacity", "off_rec_rgb", "off_rec_clamp", "off_rec_depth",
                   "off_rec_rect", "off_sorted_records", "off_tile_ranges", "off_tile_order", "off_final_T",
-                  "off_n_contrib"]
+                  "off_n_contrib", "off_pixel_stats"]
 
 
 class Layout(ctypes.Structure):
@@ -133,11 +133,12 @@ def make_cameras(cams) -> ctypes.Array:
     return arr
 
 
-def make_config(tile=(16, 16), bg=(0.0, 0.0, 0.0)) -> Config:
+def make_config(tile=(16, 16), bg=(0.0, 0.0, 0.0), pixels_per_thread=0) -> Config:
     cfg = Config()
     cfg.tile_w, cfg.tile_h = int(tile[0]), int(tile[1])
     cfg.bg[:] = [float(b) for b in bg]
     cfg.flags = 0
+    cfg.pixels_per_thread = int(pixels_per_thread)
     return cfg
 
 
@@ -235,10 +236,10 @@ class Rasterizer:
     and camera set, growing them (with headroom) when a batch needs more
     records or keys than the current capacity."""
 
-    def __init__(self, cams, tile=(16, 16), bg=(0.0, 0.0, 0.0), device="cuda", headroom=1.15):
+    def __init__(self, cams, tile=(16, 16), bg=(0.0, 0.0, 0.0), device="cuda", headroom=1.15, pixels_per_thread=0):
         self.cams_np = cams
         self.cams_c = make_cameras(cams)
-        self.cfg = make_config(tile, bg)
+        self.cfg = make_config(tile, bg, pixels_per_thread)
         self.device = device
         self.headroom = headroom
         self.cap = Capacity(0, 0)
@@ -309,4 +310,5 @@ class Rasterizer:
             tile_order=self._view(L.off_tile_order, int(L.tiles), torch.int32),
             final_T=self._view(L.off_final_T, int(L.pixels), torch.float32),
             n_contrib=self._view(L.off_n_contrib, int(L.pixels), torch.int32),
+            pixel_stats=self._view(L.off_pixel_stats, int(L.pixels), torch.int32, 2),
             counts=self._view(L.off_counts, 4, torch.int64))
