@@ -98,12 +98,12 @@ typedef struct mvgs_config {
     int32_t tile_w, tile_h;
     float bg[3];      /* background colour added with the final transmittance */
     uint32_t flags;   /* reserved, must be 0 */
-    int32_t pixels_per_thread;  /* blend threads each own this many pixels of a
-                                   tile column: 0 = automatic, else 1, 2, 4 or 8
-                                   with tile_w * tile_h / pixels_per_thread a
-                                   multiple of 32 and at most 256, and
-                                   pixels_per_thread dividing tile_h.  Results
-                                   do not depend on it. */
+    int32_t pixels_per_thread;  /* blend lanes each own this many pixels of a
+                                   tile column, so one warp blends a strip of
+                                   tile_w columns by (32 / tile_w) *
+                                   pixels_per_thread rows: 0 = automatic, else
+                                   1, 2, 4 or 8 with the strip height dividing
+                                   tile_h.  Results do not depend on it. */
 } mvgs_config;
 
 /* Capacities the caller sized `state` and `workspace` for:

@@ -141,8 +141,8 @@ mvgs_status check_config(const mvgs_config* cfg) {
     if (cfg->flags != 0) return fail(MVGS_EINVAL, "flags must be 0");
     const int ppt = cfg->pixels_per_thread;
     if (ppt != 0) {
-        const int threads = ppt > 0 ? tw * th / ppt : 0;
-        if (!(ppt == 1 || ppt == 2 || ppt == 4 || ppt == 8) || th % ppt || threads % 32 || threads > 256)
+        // a warp covers tile_w columns and (32 / tile_w) * ppt rows of a tile
+        if (!(ppt == 1 || ppt == 2 || ppt == 4 || ppt == 8) || th % ((32 / tw) * ppt))
             return fail(MVGS_EINVAL, "pixels_per_thread %d does not fit a %dx%d tile", ppt, tw, th);
     }
     return MVGS_OK;
@@ -458,7 +458,9 @@ mvgs_status mvgs_render_views(const mvgs_scene* scene, const mvgs_camera* cams, 
     ba.V = V;
     ba.tw = tw;
     ba.th = th;
-    ba.ppt = cfg->pixels_per_thread;
+    ba.ppt = blend_pixels_per_thread(tw, th, cfg->pixels_per_thread);
+    ba.strip_h = (32 / tw) * ba.ppt;
+    ba.strips = th / ba.strip_h;
     ba.tiles = P.tiles;
     ba.ranges = ranges;
     ba.order = at<uint32_t>(state, L.off_tile_order);
@@ -509,7 +511,9 @@ mvgs_status mvgs_render_views_backward(const mvgs_scene* scene, const mvgs_camer
     ba.V = V;
     ba.tw = cfg->tile_w;
     ba.th = cfg->tile_h;
-    ba.ppt = cfg->pixels_per_thread;
+    ba.ppt = blend_pixels_per_thread(ba.tw, ba.th, cfg->pixels_per_thread);
+    ba.strip_h = (32 / ba.tw) * ba.ppt;
+    ba.strips = ba.th / ba.strip_h;
     ba.tiles = P.tiles;
     ba.ranges = at<long long>(state, L.off_tile_ranges);
     ba.order = at<uint32_t>(state, L.off_tile_order);

@@ -1,27 +1,26 @@
 // Tile-based alpha blending (Eq. 1) and its backward.
 //
-// One block renders one (tile, view) pair at a time: the supplement allocates
-// "one block for each viewpoint" per tile, and Alg. 2 has the block's threads
-// fetch the tile's depth-sorted Gaussians into shared memory batch by batch,
-// blend, and synchronise.  The whole batch of views is a single persistent
-// launch over the global (view, tile) list, whatever the views' resolutions:
-// resident blocks take tiles from a queue in an order that puts the longest
-// lists first, so the heavy tiles do not form a tail.
-//
-// Each thread owns PPT pixels of one tile column (rows ly0, ly0 + R, ...), so
-// one shared-memory read of a Gaussian serves PPT pixels; pixels that have
-// stopped, or that a Gaussian does not reach, are skipped.
+// The supplement allocates "one block for each viewpoint" per tile, and
+// Alg. 2 has a tile's threads fetch its depth-sorted Gaussians into shared
+// memory batch by batch and blend them.  Here the unit of work is a strip of
+// a (tile, view) pair -- tile_w columns by (32 / tile_w) * PPT rows -- owned by
+// one warp: each lane owns PPT pixels of one column, the warp stages batches
+// of the tile's list in its own slice of shared memory, and leaves the strip
+// as soon as all its pixels have stopped.  Warps of a persistent launch take
+// strips from a queue that lists the tiles with the longest lists first, so
+// the whole batch of views (any mix of resolutions) is one launch without a
+// tail of heavy tiles, and no block-wide barrier couples unrelated strips.
 //
 // Forward per pixel (front to back): alpha = min(0.99, o G), skip alpha <
 // 1/255, stop before T (1 - alpha) < 1e-4, C += c alpha T, T *= 1 - alpha;
-// output C + T bg.  A block leaves a tile once all its pixels have stopped.
+// output C + T bg.
 //
 // Backward per pixel (back to front from the last contributor), with T
 // recovered by division:  dC/dc_i = alpha_i T_i,  dC/dalpha_i = c_i T_i -
 // S_i / (1 - alpha_i), S_i the colour blended behind i plus T_final bg.  The
-// gradients of one Gaussian are summed over the thread's pixels, then over
-// the warp by a reduce-scatter (16 shuffles for 10 values), and each lane
-// pair adds one value with one atomic.
+// gradients of one Gaussian are summed over the lane's pixels, then over the
+// warp by a reduce-scatter (16 shuffles for 10 values), and each lane pair
+// adds one value with one atomic.
 #include <mutex>
 #include <unordered_map>
 
@@ -31,90 +30,97 @@ namespace mvgs {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int BATCH = 256;  // Gaussians per shared-memory batch
+constexpr int WBATCH = 128;         // Gaussians per warp batch in shared memory
+constexpr int WARPS_PER_BLOCK = 4;
 
-struct PixelGeom {
-    int px, py0, rows;  // rows: distance between a thread's pixels
+// One warp's work item: a strip of a tile.
+struct Strip {
+    long long gt;          // global (view, tile) id, -1 when the queue is empty
     const DevCam* cam;
+    int px;                // this lane's column
+    int py0, step;         // this lane's first row and the distance between its rows
 };
 
-__device__ __forceinline__ PixelGeom pixel_geom(const BlendArgs& a, long long gt, int v) {
-    PixelGeom g;
-    g.cam = &a.cams[v];
-    const long long local = gt - g.cam->tile_base;
-    const int tx = (int)(local % g.cam->tiles_x), ty = (int)(local / g.cam->tiles_x);
-    g.rows = blockDim.x / a.tw;
-    g.px = tx * a.tw + (int)(threadIdx.x % a.tw);
-    g.py0 = ty * a.th + (int)(threadIdx.x / a.tw);
-    return g;
-}
-
-// Next tile of the queue for the whole block (-1 when the queue is empty).
-__device__ __forceinline__ long long next_tile(const BlendArgs& a, int* counter, int* s_slot, int* s_v) {
-    __syncthreads();  // every thread is done with the previous tile's shared values
-    if (threadIdx.x == 0) {
-        const int it = atomicAdd(counter, 1);
-        *s_slot = it;
-        if (it < a.tiles) *s_v = find_view(a.cams, a.V, a.order[it]);
+// Takes the next strip for the warp (lane 0 takes it, all lanes get it).
+__device__ __forceinline__ Strip next_strip(const BlendArgs& a, int* counter, int lane) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(counter, 1);
+    item = __shfl_sync(kFull, item, 0);
+    Strip s;
+    const long long total = a.tiles * a.strips;
+    if (item >= total) {
+        s.gt = -1;
+        return s;
     }
-    __syncthreads();
-    const int it = *s_slot;
-    const long long gt = it < a.tiles ? (long long)a.order[it] : -1;
-    return gt;
+    s.gt = (long long)a.order[item / a.strips];
+    const int strip = item % a.strips;
+    int v = 0;
+    if (lane == 0) v = find_view(a.cams, a.V, s.gt);
+    v = __shfl_sync(kFull, v, 0);
+    s.cam = &a.cams[v];
+    const long long local = s.gt - s.cam->tile_base;
+    const int tx = (int)(local % s.cam->tiles_x), ty = (int)(local / s.cam->tiles_x);
+    s.step = 32 / a.tw;  // thread rows of the warp
+    s.px = tx * a.tw + lane % a.tw;
+    s.py0 = ty * a.th + strip * a.strip_h + lane / a.tw;
+    return s;
 }
 
 template <int PPT>
-__global__ void __launch_bounds__(PPT >= 4 ? 128 : 256) blend_forward_kernel(BlendArgs a, int* __restrict__ counter,
-                                                           float* __restrict__ img, float* __restrict__ final_T,
-                                                           uint32_t* __restrict__ n_contrib,
-                                                           uint2* __restrict__ pixel_stats) {
-    __shared__ float2 s_xy[BATCH];
-    __shared__ float4 s_co[BATCH];
-    __shared__ float4 s_rgb[BATCH];
-    __shared__ int s_slot, s_v;
-    const int NT = blockDim.x;
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(BlendArgs a, int* __restrict__ counter,
+                                                                             float* __restrict__ img,
+                                                                             float* __restrict__ final_T,
+                                                                             uint32_t* __restrict__ n_contrib,
+                                                                             uint2* __restrict__ pixel_stats) {
+    __shared__ float2 s_xy[WARPS_PER_BLOCK][WBATCH];
+    __shared__ float4 s_co[WARPS_PER_BLOCK][WBATCH];
+    __shared__ float4 s_rgb[WARPS_PER_BLOCK][WBATCH];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float2* wxy = s_xy[w];
+    float4* wco = s_co[w];
+    float4* wrgb = s_rgb[w];
     constexpr uint32_t ALL = (1u << PPT) - 1u;
     for (;;) {
-        const long long gt = next_tile(a, counter, &s_slot, &s_v);
-        if (gt < 0) break;
-        const PixelGeom pg = pixel_geom(a, gt, s_v);
-        const DevCam& cam = *pg.cam;
-        const float fx = pg.px + 0.5f;
+        const Strip st = next_strip(a, counter, lane);
+        if (st.gt < 0) break;
+        const DevCam& cam = *st.cam;
+        const float fx = st.px + 0.5f;
+        const long long start = a.ranges[2 * st.gt], end = a.ranges[2 * st.gt + 1];
         float fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
         uint32_t last[PPT], stop[PPT], nblend[PPT];
         uint32_t done = 0;
-        const long long start = a.ranges[2 * gt], end = a.ranges[2 * gt + 1];
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
-            const int py = pg.py0 + k * pg.rows;
+            const int py = st.py0 + k * st.step;
             fy[k] = py + 0.5f;
             T[k] = 1.f;
             C0[k] = C1[k] = C2[k] = 0.f;
             last[k] = 0;
             stop[k] = (uint32_t)(end - start);  // list position where the pixel stopped
             nblend[k] = 0;
-            if (!(pg.px < cam.W && py < cam.H)) done |= 1u << k;
+            if (!(st.px < cam.W && py < cam.H)) done |= 1u << k;
         }
-        for (long long b = start; b < end; b += BATCH) {
-            if (__syncthreads_count(done == ALL) == NT) break;
-            for (int i = threadIdx.x; i < BATCH; i += NT) {
+        for (long long b = start; b < end; b += WBATCH) {
+            if (__all_sync(kFull, done == ALL)) break;
+            __syncwarp();
+            for (int i = lane; i < WBATCH; i += 32) {
                 const long long idx = b + i;
                 if (idx < end) {
                     const uint32_t r = a.sorted[idx];
-                    s_xy[i] = a.xy[r];
-                    s_co[i] = a.conic_o[r];
-                    s_rgb[i] = a.rgb_r[r];
+                    wxy[i] = a.xy[r];
+                    wco[i] = a.conic_o[r];
+                    wrgb[i] = a.rgb_r[r];
                 }
             }
-            __syncthreads();
-            const int cnt = (int)(end - b < (long long)BATCH ? end - b : (long long)BATCH);
+            __syncwarp();
+            const int cnt = (int)(end - b < (long long)WBATCH ? end - b : (long long)WBATCH);
             const uint32_t base = (uint32_t)(b - start);
             for (int j = 0; j < cnt; j++) {
-                const float2 m = s_xy[j];
-                const float4 cr = s_rgb[j];
+                const float2 m = wxy[j];
+                const float4 cr = wrgb[j];
                 const float dx = fx - m.x;
                 if (fabsf(dx) > cr.w) continue;  // outside the support for the whole column
-                const float4 co = s_co[j];
+                const float4 co = wco[j];
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
                     if ((done >> k) & 1u) continue;
@@ -126,10 +132,10 @@ __global__ void __launch_bounds__(PPT >= 4 ? 128 : 256) blend_forward_kernel(Ble
                         stop[k] = base + j + 1;
                         continue;
                     }
-                    const float w = alpha * T[k];
-                    C0[k] += cr.x * w;
-                    C1[k] += cr.y * w;
-                    C2[k] += cr.z * w;
+                    const float wgt = alpha * T[k];
+                    C0[k] += cr.x * wgt;
+                    C1[k] += cr.y * wgt;
+                    C2[k] += cr.z * wgt;
                     T[k] = Tn;
                     last[k] = base + j + 1;
                     nblend[k]++;
@@ -141,9 +147,9 @@ __global__ void __launch_bounds__(PPT >= 4 ? 128 : 256) blend_forward_kernel(Ble
         float* out = img + 3 * cam.pix_base;
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
-            const int py = pg.py0 + k * pg.rows;
-            if (pg.px < cam.W && py < cam.H) {
-                const long long p = (long long)py * cam.W + pg.px;
+            const int py = st.py0 + k * st.step;
+            if (st.px < cam.W && py < cam.H) {
+                const long long p = (long long)py * cam.W + st.px;
                 out[p] = C0[k] + T[k] * a.bg[0];
                 out[HW + p] = C1[k] + T[k] * a.bg[1];
                 out[2 * HW + p] = C2[k] + T[k] * a.bg[2];
@@ -173,30 +179,28 @@ __device__ __forceinline__ float warp_reduce_scatter16(float (&g)[16], int lane)
 }
 
 template <int PPT>
-__global__ void __launch_bounds__(PPT >= 4 ? 128 : 256) blend_backward_kernel(BlendArgs a, int* __restrict__ counter,
-                                                            const float* __restrict__ dimg,
-                                                            const float* __restrict__ final_T,
-                                                            const uint32_t* __restrict__ n_contrib,
-                                                            float* __restrict__ rec_grad) {
-    __shared__ float2 s_xy[BATCH];
-    __shared__ float4 s_co[BATCH];
-    __shared__ float4 s_rgb[BATCH];
-    __shared__ uint32_t s_rid[BATCH];
-    __shared__ int s_slot, s_v;
-    __shared__ uint32_t s_max;
-    const int NT = blockDim.x;
-    const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(BlendArgs a, int* __restrict__ counter,
+                                                                              const float* __restrict__ dimg,
+                                                                              const float* __restrict__ final_T,
+                                                                              const uint32_t* __restrict__ n_contrib,
+                                                                              float* __restrict__ rec_grad) {
+    __shared__ float2 s_xy[WARPS_PER_BLOCK][WBATCH];
+    __shared__ float4 s_co[WARPS_PER_BLOCK][WBATCH];
+    __shared__ float4 s_rgb[WARPS_PER_BLOCK][WBATCH];
+    __shared__ uint32_t s_rid[WARPS_PER_BLOCK][WBATCH];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float2* wxy = s_xy[w];
+    float4* wco = s_co[w];
+    float4* wrgb = s_rgb[w];
+    uint32_t* wrid = s_rid[w];
     // value this lane adds after the reduce-scatter (lane pairs share one)
     const int my_val = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
     const bool adder = (lane & 1) == 0 && my_val < 10;
     for (;;) {
-        const long long gt = next_tile(a, counter, &s_slot, &s_v);
-        if (gt < 0) break;
-        if (threadIdx.x == 0) s_max = 0;
-        __syncthreads();
-        const PixelGeom pg = pixel_geom(a, gt, s_v);
-        const DevCam& cam = *pg.cam;
-        const float fx = pg.px + 0.5f;
+        const Strip st = next_strip(a, counter, lane);
+        if (st.gt < 0) break;
+        const DevCam& cam = *st.cam;
+        const float fx = st.px + 0.5f;
         const long long HW = (long long)cam.W * cam.H;
         const float* din = dimg + 3 * cam.pix_base;
         float fy[PPT], T[PPT], d0[PPT], d1[PPT], d2[PPT], S0[PPT], S1[PPT], S2[PPT];
@@ -204,13 +208,13 @@ __global__ void __launch_bounds__(PPT >= 4 ? 128 : 256) blend_backward_kernel(Bl
         uint32_t mylast = 0;
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
-            const int py = pg.py0 + k * pg.rows;
+            const int py = st.py0 + k * st.step;
             fy[k] = py + 0.5f;
             T[k] = 1.f;
             d0[k] = d1[k] = d2[k] = 0.f;
             last[k] = 0;
-            if (pg.px < cam.W && py < cam.H) {
-                const long long p = (long long)py * cam.W + pg.px;
+            if (st.px < cam.W && py < cam.H) {
+                const long long p = (long long)py * cam.W + st.px;
                 d0[k] = din[p];
                 d1[k] = din[HW + p];
                 d2[k] = din[2 * HW + p];
@@ -223,35 +227,33 @@ __global__ void __launch_bounds__(PPT >= 4 ? 128 : 256) blend_backward_kernel(Bl
             S2[k] = T[k] * a.bg[2];
             mylast = last[k] > mylast ? last[k] : mylast;
         }
-        atomicMax(&s_max, mylast);
-        __syncthreads();
-        const uint32_t maxlast = s_max;
-        const long long start = a.ranges[2 * gt];
-        for (uint32_t b = 0; b < maxlast; b += BATCH) {
-            __syncthreads();
-            for (int i = threadIdx.x; i < BATCH; i += NT) {
+        const uint32_t maxlast = __reduce_max_sync(kFull, mylast);
+        const long long start = a.ranges[2 * st.gt];
+        for (uint32_t b = 0; b < maxlast; b += WBATCH) {
+            __syncwarp();
+            for (int i = lane; i < WBATCH; i += 32) {
                 const long long pos = (long long)maxlast - 1 - b - i;  // list position of slot i
                 if (pos >= 0) {
                     const uint32_t r = a.sorted[start + pos];
-                    s_rid[i] = r;
-                    s_xy[i] = a.xy[r];
-                    s_co[i] = a.conic_o[r];
-                    s_rgb[i] = a.rgb_r[r];
+                    wrid[i] = r;
+                    wxy[i] = a.xy[r];
+                    wco[i] = a.conic_o[r];
+                    wrgb[i] = a.rgb_r[r];
                 }
             }
-            __syncthreads();
-            const int cnt = (int)(maxlast - b < (uint32_t)BATCH ? maxlast - b : (uint32_t)BATCH);
+            __syncwarp();
+            const int cnt = (int)(maxlast - b < (uint32_t)WBATCH ? maxlast - b : (uint32_t)WBATCH);
             for (int j = 0; j < cnt; j++) {
                 const uint32_t pos = maxlast - 1 - b - j;
                 float g[16];
 #pragma unroll
                 for (int i = 0; i < 16; i++) g[i] = 0.f;
                 bool any = false;
-                const float2 m = s_xy[j];
-                const float4 cr = s_rgb[j];
+                const float2 m = wxy[j];
+                const float4 cr = wrgb[j];
                 const float dx = fx - m.x;
                 if (pos < mylast && fabsf(dx) <= cr.w) {
-                    const float4 co = s_co[j];
+                    const float4 co = wco[j];
 #pragma unroll
                     for (int k = 0; k < PPT; k++) {
                         if (pos >= last[k]) continue;
@@ -261,15 +263,15 @@ __global__ void __launch_bounds__(PPT >= 4 ? 128 : 256) blend_backward_kernel(Bl
                         any = true;
                         const float inv = __frcp_rn(1.f - alpha);
                         T[k] *= inv;  // transmittance in front of this Gaussian
-                        const float w = alpha * T[k];
-                        g[6] += d0[k] * w;
-                        g[7] += d1[k] * w;
-                        g[8] += d2[k] * w;
+                        const float wgt = alpha * T[k];
+                        g[6] += d0[k] * wgt;
+                        g[7] += d1[k] * wgt;
+                        g[8] += d2[k] * wgt;
                         const float dLda = d0[k] * (cr.x * T[k] - S0[k] * inv) + d1[k] * (cr.y * T[k] - S1[k] * inv) +
                                            d2[k] * (cr.z * T[k] - S2[k] * inv);
-                        S0[k] += cr.x * w;
-                        S1[k] += cr.y * w;
-                        S2[k] += cr.z * w;
+                        S0[k] += cr.x * wgt;
+                        S1[k] += cr.y * wgt;
+                        S2[k] += cr.z * wgt;
                         if (co.w * G < kAlphaMax) {  // below the clamp alpha = o G
                             const float dLdp = dLda * alpha;  // dL/d power = dL/dalpha o G
                             const float gx = dLdp * (co.x * dx + co.y * dy);
@@ -286,57 +288,53 @@ __global__ void __launch_bounds__(PPT >= 4 ? 128 : 256) blend_backward_kernel(Bl
                 }
                 if (__ballot_sync(kFull, any) == 0u) continue;
                 const float sum = warp_reduce_scatter16(g, lane);
-                if (adder) atomicAdd(rec_grad + (size_t)kGradStride * s_rid[j] + my_val, sum);
+                if (adder) atomicAdd(rec_grad + (size_t)kGradStride * wrid[j] + my_val, sum);
             }
         }
     }
 }
 
-// threads per block and pixels per thread for a tile size (tile sides 8, 16
-// or 32 with at most 512 pixels: the thread count is a multiple of 32 and
-// divides evenly into tile rows); a requested pixels-per-thread was checked
-// by the caller
-void blend_shape(int tw, int th, int req, int& threads, int& ppt) {
-    const int pix = tw * th;
-    ppt = req > 0 ? req : (pix >= 128 ? 4 : 2);
-    threads = pix / ppt;
-}
-
-// Resident blocks over the whole GPU for a kernel at a block size (cached).
-int persistent_blocks(const void* kernel, int threads) {
+// Resident blocks over the whole GPU for a kernel (cached per kernel).
+int persistent_blocks(const void* kernel) {
     static std::mutex mu;
     static std::unordered_map<const void*, int> cache;
     std::lock_guard<std::mutex> lk(mu);
-    const auto key = static_cast<const void*>(static_cast<const char*>(kernel) + threads);
-    auto it = cache.find(key);
+    auto it = cache.find(kernel);
     if (it != cache.end()) return it->second;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * WARPS_PER_BLOCK, 0);
     const int n = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-    cache[key] = n;
+    cache[kernel] = n;
     return n;
 }
 
 template <class K>
-unsigned grid_for(K kernel, int threads, long long tiles) {
-    const long long n = persistent_blocks(reinterpret_cast<const void*>(kernel), threads);
-    return (unsigned)(tiles < n ? tiles : n);
+unsigned grid_for(K kernel, long long items) {
+    const long long blocks = (items + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
+    const long long n = persistent_blocks(reinterpret_cast<const void*>(kernel));
+    return (unsigned)(blocks < n ? blocks : n);
 }
 
 }  // namespace
 
+int blend_pixels_per_thread(int tw, int th, int req) {
+    if (req > 0) return req;
+    for (int p = 4; p >= 1; p >>= 1)
+        if (th % ((32 / tw) * p) == 0) return p;
+    return 1;
+}
+
 void launch_blend_forward(const BlendArgs& a, int* counter, float* img, float* final_T, uint32_t* n_contrib,
                           uint2* pixel_stats, cudaStream_t s) {
     if (a.tiles == 0) return;
-    int threads, ppt;
-    blend_shape(a.tw, a.th, a.ppt, threads, ppt);
     cudaMemsetAsync(counter, 0, sizeof(int), s);
+    const long long items = a.tiles * a.strips;
 #define MVGS_BF(P)                                                                                               \
-    blend_forward_kernel<P><<<grid_for(blend_forward_kernel<P>, threads, a.tiles), threads, 0, s>>>(            \
+    blend_forward_kernel<P><<<grid_for(blend_forward_kernel<P>, items), 32 * WARPS_PER_BLOCK, 0, s>>>(          \
         a, counter, img, final_T, n_contrib, pixel_stats)
-    switch (ppt) {
+    switch (a.ppt) {
         case 1: MVGS_BF(1); break;
         case 2: MVGS_BF(2); break;
         case 8: MVGS_BF(8); break;
@@ -349,13 +347,12 @@ void launch_blend_forward(const BlendArgs& a, int* counter, float* img, float* f
 void launch_blend_backward(const BlendArgs& a, int* counter, const float* dimg, const float* final_T,
                            const uint32_t* n_contrib, float* rec_grad, cudaStream_t s) {
     if (a.tiles == 0) return;
-    int threads, ppt;
-    blend_shape(a.tw, a.th, a.ppt, threads, ppt);
     cudaMemsetAsync(counter, 0, sizeof(int), s);
+    const long long items = a.tiles * a.strips;
 #define MVGS_BB(P)                                                                                               \
-    blend_backward_kernel<P><<<grid_for(blend_backward_kernel<P>, threads, a.tiles), threads, 0, s>>>(          \
+    blend_backward_kernel<P><<<grid_for(blend_backward_kernel<P>, items), 32 * WARPS_PER_BLOCK, 0, s>>>(        \
         a, counter, dimg, final_T, n_contrib, rec_grad)
-    switch (ppt) {
+    switch (a.ppt) {
         case 1: MVGS_BB(1); break;
         case 2: MVGS_BB(2); break;
         case 8: MVGS_BB(8); break;

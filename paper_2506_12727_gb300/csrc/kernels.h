@@ -98,7 +98,9 @@ struct BlendArgs {
     const DevCam* cams;
     int V;
     int tw, th;
-    int ppt;                 // pixels per thread (0 = automatic)
+    int ppt;                 // pixels per lane (resolved, 1..8)
+    int strip_h;             // rows of a warp's strip: (32 / tw) * ppt
+    int strips;              // strips per tile: th / strip_h
     long long tiles;
     const long long* ranges;
     const uint32_t* order;   // tiles in processing order (longest lists first)
@@ -108,6 +110,8 @@ struct BlendArgs {
     const float4* rgb_r;
     float bg[3];
 };
+// Pixels per lane for a tile size (req > 0: the caller's choice, checked).
+int blend_pixels_per_thread(int tw, int th, int req);
 // Persistent launches; `counter` is one device int of scratch (reset here).
 void launch_blend_forward(const BlendArgs& a, int* counter, float* img, float* final_T, uint32_t* n_contrib,
                           uint2* pixel_stats, cudaStream_t s);
