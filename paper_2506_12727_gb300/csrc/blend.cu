@@ -11,6 +11,11 @@
 // the whole batch of views (any mix of resolutions) is one launch without a
 // tail of heavy tiles, and no block-wide barrier couples unrelated strips.
 //
+// Each staged batch keeps only the Gaussians whose support and alpha >= 1/255
+// region reach a pixel centre of the strip (an exact test of the quadratic
+// form over the strip's rectangle), compacted with a ballot; the list
+// positions are kept for the per-pixel bookkeeping.
+//
 // Forward per pixel (front to back): alpha = min(0.99, o G), skip alpha <
 // 1/255, stop before T (1 - alpha) < 1e-4, C += c alpha T, T *= 1 - alpha;
 // output C + T bg.
@@ -39,6 +44,7 @@ struct Strip {
     const DevCam* cam;
     int px;                // this lane's column
     int py0, step;         // this lane's first row and the distance between its rows
+    float sx0, sx1, sy0, sy1;  // pixel-centre bounds of the strip inside the image
 };
 
 // Takes the next strip for the warp (lane 0 takes it, all lanes get it).
@@ -63,6 +69,11 @@ __device__ __forceinline__ Strip next_strip(const BlendArgs& a, int* counter, in
     s.step = 32 / a.tw;  // thread rows of the warp
     s.px = tx * a.tw + lane % a.tw;
     s.py0 = ty * a.th + strip * a.strip_h + lane / a.tw;
+    const int x0 = tx * a.tw, y0 = ty * a.th + strip * a.strip_h;
+    s.sx0 = x0 + 0.5f;
+    s.sx1 = (float)min(x0 + a.tw, s.cam->W) - 0.5f;
+    s.sy0 = y0 + 0.5f;
+    s.sy1 = (float)min(y0 + a.strip_h, s.cam->H) - 0.5f;
     return s;
 }
 
@@ -75,10 +86,13 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(Ble
     __shared__ float2 s_xy[WARPS_PER_BLOCK][WBATCH];
     __shared__ float4 s_co[WARPS_PER_BLOCK][WBATCH];
     __shared__ float4 s_rgb[WARPS_PER_BLOCK][WBATCH];
+    __shared__ uint32_t s_pos[WARPS_PER_BLOCK][WBATCH];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
     float2* wxy = s_xy[w];
     float4* wco = s_co[w];
     float4* wrgb = s_rgb[w];
+    uint32_t* wpos = s_pos[w];
     constexpr uint32_t ALL = (1u << PPT) - 1u;
     for (;;) {
         const Strip st = next_strip(a, counter, lane);
@@ -102,34 +116,48 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(Ble
         }
         for (long long b = start; b < end; b += WBATCH) {
             if (__all_sync(kFull, done == ALL)) break;
+            // stage the Gaussians of this batch that can reach a pixel of the strip
             __syncwarp();
-            for (int i = lane; i < WBATCH; i += 32) {
-                const long long idx = b + i;
+            int n = 0;
+            for (int i0 = 0; i0 < WBATCH; i0 += 32) {
+                const long long idx = b + i0 + lane;
+                bool hit = false;
+                float2 m;
+                float4 co, cr;
                 if (idx < end) {
                     const uint32_t r = a.sorted[idx];
-                    wxy[i] = a.xy[r];
-                    wco[i] = a.conic_o[r];
-                    wrgb[i] = a.rgb_r[r];
+                    m = a.xy[r];
+                    co = a.conic_o[r];
+                    cr = a.rgb_r[r];
+                    hit = rect_reaches(st.sx0 - m.x, st.sx1 - m.x, st.sy0 - m.y, st.sy1 - m.y, co, cr.w);
                 }
+                const uint32_t bal = __ballot_sync(kFull, hit);
+                if (hit) {
+                    const int slot = n + __popc(bal & lt);
+                    wxy[slot] = m;
+                    wco[slot] = co;
+                    wrgb[slot] = cr;
+                    wpos[slot] = (uint32_t)(idx - start);
+                }
+                n += __popc(bal);
             }
             __syncwarp();
-            const int cnt = (int)(end - b < (long long)WBATCH ? end - b : (long long)WBATCH);
-            const uint32_t base = (uint32_t)(b - start);
-            for (int j = 0; j < cnt; j++) {
+            for (int j = 0; j < n; j++) {
                 const float2 m = wxy[j];
                 const float4 cr = wrgb[j];
                 const float dx = fx - m.x;
                 if (fabsf(dx) > cr.w) continue;  // outside the support for the whole column
                 const float4 co = wco[j];
+                const uint32_t pos = wpos[j];
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
                     if ((done >> k) & 1u) continue;
-                    float alpha, G;
-                    if (!pair_eval(dx, fy[k] - m.y, co, cr.w, alpha, G)) continue;
+                    float alpha, G, ax, ay;
+                    if (!pair_eval(dx, fy[k] - m.y, co, cr.w, alpha, G, ax, ay)) continue;
                     const float Tn = T[k] * (1.f - alpha);
                     if (Tn < kTMin) {
                         done |= 1u << k;
-                        stop[k] = base + j + 1;
+                        stop[k] = pos + 1;
                         continue;
                     }
                     const float wgt = alpha * T[k];
@@ -137,7 +165,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(Ble
                     C1[k] += cr.y * wgt;
                     C2[k] += cr.z * wgt;
                     T[k] = Tn;
-                    last[k] = base + j + 1;
+                    last[k] = pos + 1;
                     nblend[k]++;
                 }
                 if (done == ALL) break;
@@ -188,11 +216,14 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(Bl
     __shared__ float4 s_co[WARPS_PER_BLOCK][WBATCH];
     __shared__ float4 s_rgb[WARPS_PER_BLOCK][WBATCH];
     __shared__ uint32_t s_rid[WARPS_PER_BLOCK][WBATCH];
+    __shared__ uint32_t s_pos[WARPS_PER_BLOCK][WBATCH];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
     float2* wxy = s_xy[w];
     float4* wco = s_co[w];
     float4* wrgb = s_rgb[w];
     uint32_t* wrid = s_rid[w];
+    uint32_t* wpos = s_pos[w];
     // value this lane adds after the reduce-scatter (lane pairs share one)
     const int my_val = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
     const bool adder = (lane & 1) == 0 && my_val < 10;
@@ -203,7 +234,9 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(Bl
         const float fx = st.px + 0.5f;
         const long long HW = (long long)cam.W * cam.H;
         const float* din = dimg + 3 * cam.pix_base;
-        float fy[PPT], T[PPT], d0[PPT], d1[PPT], d2[PPT], S0[PPT], S1[PPT], S2[PPT];
+        // per pixel: T in front of the current Gaussian, dL/dC, and
+        // U = dL/dC . (colour blended behind the current Gaussian + T_final bg)
+        float fy[PPT], T[PPT], d0[PPT], d1[PPT], d2[PPT], U[PPT];
         uint32_t last[PPT];
         uint32_t mylast = 0;
 #pragma unroll
@@ -221,30 +254,42 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(Bl
                 T[k] = final_T[cam.pix_base + p];
                 last[k] = n_contrib[cam.pix_base + p];
             }
-            // colour blended behind the current Gaussian, starting with the background
-            S0[k] = T[k] * a.bg[0];
-            S1[k] = T[k] * a.bg[1];
-            S2[k] = T[k] * a.bg[2];
+            U[k] = T[k] * (d0[k] * a.bg[0] + d1[k] * a.bg[1] + d2[k] * a.bg[2]);
             mylast = last[k] > mylast ? last[k] : mylast;
         }
         const uint32_t maxlast = __reduce_max_sync(kFull, mylast);
         const long long start = a.ranges[2 * st.gt];
         for (uint32_t b = 0; b < maxlast; b += WBATCH) {
+            // stage, back to front, the Gaussians that can reach the strip
             __syncwarp();
-            for (int i = lane; i < WBATCH; i += 32) {
-                const long long pos = (long long)maxlast - 1 - b - i;  // list position of slot i
+            int n = 0;
+            for (int i0 = 0; i0 < WBATCH; i0 += 32) {
+                const long long pos = (long long)maxlast - 1 - b - i0 - lane;
+                bool hit = false;
+                uint32_t r = 0;
+                float2 m;
+                float4 co, cr;
                 if (pos >= 0) {
-                    const uint32_t r = a.sorted[start + pos];
-                    wrid[i] = r;
-                    wxy[i] = a.xy[r];
-                    wco[i] = a.conic_o[r];
-                    wrgb[i] = a.rgb_r[r];
+                    r = a.sorted[start + pos];
+                    m = a.xy[r];
+                    co = a.conic_o[r];
+                    cr = a.rgb_r[r];
+                    hit = rect_reaches(st.sx0 - m.x, st.sx1 - m.x, st.sy0 - m.y, st.sy1 - m.y, co, cr.w);
                 }
+                const uint32_t bal = __ballot_sync(kFull, hit);
+                if (hit) {
+                    const int slot = n + __popc(bal & lt);
+                    wrid[slot] = r;
+                    wxy[slot] = m;
+                    wco[slot] = co;
+                    wrgb[slot] = cr;
+                    wpos[slot] = (uint32_t)pos;
+                }
+                n += __popc(bal);
             }
             __syncwarp();
-            const int cnt = (int)(maxlast - b < (uint32_t)WBATCH ? maxlast - b : (uint32_t)WBATCH);
-            for (int j = 0; j < cnt; j++) {
-                const uint32_t pos = maxlast - 1 - b - j;
+            for (int j = 0; j < n; j++) {
+                const uint32_t pos = wpos[j];
                 float g[16];
 #pragma unroll
                 for (int i = 0; i < 16; i++) g[i] = 0.f;
@@ -258,8 +303,8 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(Bl
                     for (int k = 0; k < PPT; k++) {
                         if (pos >= last[k]) continue;
                         const float dy = fy[k] - m.y;
-                        float alpha, G;
-                        if (!pair_eval(dx, dy, co, cr.w, alpha, G)) continue;
+                        float alpha, G, ax, ay;
+                        if (!pair_eval(dx, dy, co, cr.w, alpha, G, ax, ay)) continue;
                         any = true;
                         const float inv = __frcp_rn(1.f - alpha);
                         T[k] *= inv;  // transmittance in front of this Gaussian
@@ -267,20 +312,19 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(Bl
                         g[6] += d0[k] * wgt;
                         g[7] += d1[k] * wgt;
                         g[8] += d2[k] * wgt;
-                        const float dLda = d0[k] * (cr.x * T[k] - S0[k] * inv) + d1[k] * (cr.y * T[k] - S1[k] * inv) +
-                                           d2[k] * (cr.z * T[k] - S2[k] * inv);
-                        S0[k] += cr.x * wgt;
-                        S1[k] += cr.y * wgt;
-                        S2[k] += cr.z * wgt;
+                        const float dc = d0[k] * cr.x + d1[k] * cr.y + d2[k] * cr.z;
+                        const float dLda = T[k] * dc - U[k] * inv;
+                        U[k] += dc * wgt;
                         if (co.w * G < kAlphaMax) {  // below the clamp alpha = o G
                             const float dLdp = dLda * alpha;  // dL/d power = dL/dalpha o G
-                            const float gx = dLdp * (co.x * dx + co.y * dy);
-                            const float gy = dLdp * (co.z * dy + co.y * dx);
+                            const float gx = dLdp * ax;       // d power / d mean2d = (ax, ay)
+                            const float gy = dLdp * ay;
+                            const float h = -0.5f * dLdp;
                             g[0] += gx;
                             g[1] += gy;
-                            g[2] += -0.5f * dLdp * dx * dx;
-                            g[3] += -dLdp * dx * dy;
-                            g[4] += -0.5f * dLdp * dy * dy;
+                            g[2] += h * dx * dx;
+                            g[3] += 2.f * h * dx * dy;
+                            g[4] += h * dy * dy;
                             g[5] += dLda * G;
                             g[9] += sqrtf(gx * gx + gy * gy);
                         }

@@ -56,16 +56,53 @@ __device__ __forceinline__ int find_view(const DevCam* cams, int V, long long gt
 }
 
 // The blend decision and opacity of one (pixel, Gaussian) pair (Eq. 1 with
-// the 3DGS clamp and skip rules and the per-pixel support rule).  Everything
-// is evaluated unconditionally so callers can stay branch-free; the return
-// value says whether the Gaussian takes part at this pixel, alpha and the
-// Gaussian falloff G are valid when it does.  The forward and the backward
-// call this same function, so both take the same decision for every pair.
-__device__ __forceinline__ bool pair_eval(float dx, float dy, float4 co, float radius, float& alpha, float& G) {
-    const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
+// the 3DGS clamp and skip rules and the per-pixel support rule), d = pixel
+// centre minus projected mean, conic (A, B, C) so that the exponent is
+// power = -(A dx^2 + 2 B dx dy + C dy^2) / 2 = -(dx ax + dy ay) / 2 with
+// (ax, ay) = (A dx + B dy, B dx + C dy).  Everything is evaluated
+// unconditionally; the return value says whether the Gaussian takes part at
+// this pixel, and alpha, G = exp(power) and (ax, ay) are valid when it does.
+// The forward and the backward call this same function, so both take the
+// same decision for every pair.
+__device__ __forceinline__ bool pair_eval(float dx, float dy, float4 co, float radius, float& alpha, float& G,
+                                          float& ax, float& ay) {
+    ax = co.x * dx + co.y * dy;
+    ay = co.y * dx + co.z * dy;
+    const float power = -0.5f * (dx * ax + dy * ay);
     G = __expf(power);
     alpha = fminf(kAlphaMax, co.w * G);
     return fabsf(dx) <= radius && fabsf(dy) <= radius && power <= 0.f && alpha >= kAlphaMin;
+}
+
+// Whether a Gaussian can pass the support rule and alpha >= 1/255 at any
+// pixel centre of the rectangle [x0, x1] x [y0, y1] (centre coordinates,
+// relative to the projected mean).  The exponent is largest where the
+// quadratic form q = A dx^2 + 2 B dx dy + C dy^2 is smallest; over a
+// rectangle that is 0 if it holds the mean, else on an edge, where q is a
+// 1D quadratic minimised in closed form.  alpha >= 1/255 needs
+// q <= 2 ln(255 o); the margin keeps the test a superset of what any pixel's
+// float32 evaluation lets through.
+__device__ __forceinline__ bool rect_reaches(float x0, float x1, float y0, float y1, float4 co, float radius) {
+    if (x0 > radius || x1 < -radius || y0 > radius || y1 < -radius) return false;
+    const float lvl = 2.f * __logf(255.f * co.w);
+    if (!(lvl > 0.f)) return false;
+    if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return true;
+    const float A = co.x, B = co.y, C = co.z;
+    auto q = [&](float x, float y) { return A * x * x + 2.f * B * x * y + C * y * y; };
+    // edges x = x0, x = x1: minimise over y in [y0, y1]
+    const float iC = 1.f / C, iA = 1.f / A;
+    float best = 3.4e38f;
+    {
+        const float ya = fminf(fmaxf(-B * x0 * iC, y0), y1);
+        const float yb = fminf(fmaxf(-B * x1 * iC, y0), y1);
+        best = fminf(best, fminf(q(x0, ya), q(x1, yb)));
+    }
+    {
+        const float xa = fminf(fmaxf(-B * y0 * iA, x0), x1);
+        const float xb = fminf(fmaxf(-B * y1 * iA, x0), x1);
+        best = fminf(best, fminf(q(xa, y0), q(xb, y1)));
+    }
+    return best <= lvl * 1.001f + 1e-3f;
 }
 
 }  // namespace mvgs
