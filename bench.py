@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--tile", default="auto", help="WxH, or auto (timed choice before the measured steps)")
     ap.add_argument("--ppt", type=int, default=0, help="blend pixels per thread (0 = automatic)")
     ap.add_argument("--no-loop", action="store_true", help="skip the per-view launch loop")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -128,7 +128,6 @@ def run_ours(args, rank, world):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    tile = tuple(int(x) for x in args.tile.split("x"))
     scene, cams, extra = synth.workload(args.workload)
     V, n = cams.V, scene.n
     targets = synth.make_targets(cams)
@@ -138,6 +137,13 @@ def run_ours(args, rank, world):
               ("means", "log_scales", "quats", "opacity_logits", "sh")}
     tgt = torch.tensor(synth.pack_images(targets), device=dev)
     sc = mvgs.make_scene(params, scene.sh_degree)
+    tuning = None
+    if args.tile == "auto":
+        from paper_2506_12727_gb300.autotune import autotune
+        tile, ppt, tuning = autotune(sc, cams, params)
+        args.ppt = ppt
+        args.tile = f"{tile[0]}x{tile[1]}"
+    tile = tuple(int(x) for x in args.tile.split("x"))
     rz = mvgs.Rasterizer(cams, tile=tile, pixels_per_thread=args.ppt)
     grads = {k: torch.empty_like(v) for k, v in params.items()}
     dssim_ws = torch.empty(mvgs.dssim_workspace_size(hw), dtype=torch.uint8, device=dev)
@@ -248,7 +254,7 @@ def run_ours(args, rank, world):
         "config": {"workload": args.workload, "gaussians": n, "sh_degree": scene.sh_degree, "views": V,
                    "resolutions": sorted({f"{w}x{h}" for w, h in zip(cams.width, cams.height)}),
                    "loss": "0.8 L1 + 0.2 D-SSIM (11x11, sigma 1.5)", "adc": True, "tile": args.tile,
-                   "pixels_per_thread": args.ppt or "auto",
+                   "pixels_per_thread": args.ppt or "auto", "autotune_ms": tuning,
                    "records": needed[0], "keys": needed[1],
                    "l2": "512 MB buffer written between timed steps (L2 is 129 MB); per-step working set > 1 GB",
                    "parallelism": "replicas" if world > 1 else "single"},

@@ -88,9 +88,9 @@ typedef struct mvgs_scene {
     const float* sh;             /* [n, (d+1)^2, 3] */
 } mvgs_scene;
 
-/* Render settings.  tile_w x tile_h pixels form one tile; one CUDA block
- * renders one (tile, view).  Supported: tile_w and tile_h each 8, 16 or 32,
- * with tile_w * tile_h <= 512 (8x8, 16x16, 16x32, 32x16, ...).  The rendered
+/* Render settings.  tile_w x tile_h pixels form one tile: the unit the
+ * Gaussians are binned and sorted by.  Blending works on warp-sized strips of
+ * a tile.  Supported: tile_w 8, 16 or 32 and tile_h 8, 16, 32 or 64.  The rendered
  * image does not depend on the tile size: a pixel blends a Gaussian only when
  * it lies within the Gaussian's radius on both axes, and every tile that
  * holds such a pixel lists the Gaussian. */

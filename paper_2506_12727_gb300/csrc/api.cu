@@ -135,9 +135,8 @@ struct Plan {
 mvgs_status check_config(const mvgs_config* cfg) {
     if (!cfg) return fail(MVGS_EINVAL, "config is NULL");
     const int tw = cfg->tile_w, th = cfg->tile_h;
-    const bool side_ok = (tw == 8 || tw == 16 || tw == 32) && (th == 8 || th == 16 || th == 32);
-    if (!side_ok || tw * th > 512)
-        return fail(MVGS_EINVAL, "unsupported tile %dx%d (sides 8, 16 or 32, at most 512 pixels)", tw, th);
+    const bool side_ok = (tw == 8 || tw == 16 || tw == 32) && (th == 8 || th == 16 || th == 32 || th == 64);
+    if (!side_ok) return fail(MVGS_EINVAL, "unsupported tile %dx%d (width 8, 16 or 32; height 8 to 64)", tw, th);
     if (cfg->flags != 0) return fail(MVGS_EINVAL, "flags must be 0");
     const int ppt = cfg->pixels_per_thread;
     if (ppt != 0) {

@@ -62,8 +62,9 @@ def test_layout_is_aligned_and_consistent(lib):
 
 
 @pytest.mark.parametrize("tile,ok", [((16, 16), True), ((8, 8), True), ((16, 32), True), ((32, 16), True),
-                                     ((8, 32), True), ((12, 16), False), ((4, 16), False), ((32, 32), False),
-                                     ((8, 4), False), ((24, 8), False)])
+                                     ((8, 32), True), ((32, 32), True), ((16, 64), True), ((32, 64), True),
+                                     ((12, 16), False), ((4, 16), False), ((64, 32), False), ((8, 4), False),
+                                     ((24, 8), False), ((16, 128), False)])
 def test_tile_validation(lib, tile, ok):
     cams = lib.make_cameras(synth.make_cameras([(64, 64)]))
     if ok:

@@ -158,7 +158,8 @@ def test_backward_matches_oracle(case):
 def test_image_is_independent_of_tile_size(cuda_lib):
     scene, cams = CASES["multiview_sh3_ragged"]
     imgs = []
-    for tile in ((8, 8), (16, 16), (16, 32), (32, 16), (8, 16), (32, 8), (8, 32), (16, 8)):
+    for tile in ((8, 8), (16, 16), (16, 32), (32, 16), (8, 16), (32, 8), (8, 32), (16, 8), (32, 32), (16, 64),
+                 (32, 64)):
         _, _, _, img = gpu_forward(cuda_lib, scene, cams, tile, (0.3, 0.3, 0.3))
         imgs.append(img.cpu().numpy())
     for im in imgs[1:]:
