@@ -34,14 +34,16 @@ WORKLOAD = "multiview_500k_4x1264x832"
 LAMBDA = 0.2
 METRIC = "fwd+bwd views/s (batched multi-view vs per-view loop) at oracle tol; serve p50/p99"
 FP32_LANES_PER_SM = 128
-# Algorithmic FP32 work of the blend kernels per (pixel, list entry) pair.
-# Examining a pair: offsets, the quadratic form, exp argument, opacity
-# product and clamp (14 FLOP, plus one ex2).  Blending it (forward):
-# transmittance update, weight and three colour FMAs (8 FLOP).  Its gradient
-# (backward): transmittance recovery, colour, alpha, power, mean2d, conic,
-# opacity and E1 terms (50 FLOP, counted from the chain rule of Eq. 1).
-FWD_FLOP_PER_EXAMINED, FWD_FLOP_PER_BLENDED = 14, 8
-BWD_FLOP_PER_EXAMINED, BWD_FLOP_PER_BLENDED = 14, 50
+# Algorithmic FP32 work of the blend kernels, counted only on the (pixel,
+# Gaussian) pairs Eq. 1 actually blends (so it does not depend on the tile
+# size or on how many list entries an implementation inspects): evaluating
+# the pair (offsets, quadratic form, exponent, opacity product and clamp:
+# 14 FLOP, plus one ex2), then blending it in the forward (transmittance,
+# weight, three colour FMAs: 8 FLOP) or differentiating it in the backward
+# (transmittance recovery, colour, alpha, exponent, mean2d, conic, opacity and
+# E1 terms: 50 FLOP, counted from the chain rule of Eq. 1).
+FWD_FLOP_PER_BLENDED = 14 + 8
+BWD_FLOP_PER_BLENDED = 14 + 50
 
 
 def parse():
@@ -306,17 +308,10 @@ def roofline(stages, args, needed, rz, clk):
     if dom in ("blend_forward", "blend_backward"):
         rec = rz.records()
         stats = rec["pixel_stats"].to(torch.int64)
-        examined = stats[:, 0].sum().item()   # (pixel, entry) pairs the forward examined
         blended = stats[:, 1].sum().item()    # (pixel, Gaussian) pairs blended
-        before_last = rec["n_contrib"].to(torch.int64).sum().item()  # pairs the backward examines
-        if dom == "blend_forward":
-            flops = FWD_FLOP_PER_EXAMINED * examined + FWD_FLOP_PER_BLENDED * blended
-            what = (f"{FWD_FLOP_PER_EXAMINED} FLOP x {examined} examined + {FWD_FLOP_PER_BLENDED} FLOP x {blended} "
-                    "blended (pixel, entry) pairs")
-        else:
-            flops = BWD_FLOP_PER_EXAMINED * before_last + BWD_FLOP_PER_BLENDED * blended
-            what = (f"{BWD_FLOP_PER_EXAMINED} FLOP x {before_last} examined + {BWD_FLOP_PER_BLENDED} FLOP x "
-                    f"{blended} blended (pixel, entry) pairs")
+        per = FWD_FLOP_PER_BLENDED if dom == "blend_forward" else BWD_FLOP_PER_BLENDED
+        flops = per * blended
+        what = f"{per} FLOP x {blended} blended (pixel, Gaussian) pairs" 
         mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1455.0)
         peak = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
         ach = flops / (ms_launch / 1e3) / 1e12
