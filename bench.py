@@ -224,9 +224,16 @@ def run_ours(args, rank, world):
                             torch.empty(1, device=dev), torch.empty(int(off[v + 1] - off[v]), device=dev),
                             torch.empty(mvgs.dssim_workspace_size(hv), dtype=torch.uint8, device=dev)))
 
+        acc_grads = {k: torch.zeros_like(v) for k, v in params.items()}
+
         def loop_step():
+            # a per-view training step sums the views' parameter gradients
+            for g in acc_grads.values():
+                g.zero_()
             for rv, tv, hv, lv, dv, wv in singles:
                 step(rv, sc, tv, hv, lv, dv, wv)
+                for k in acc_grads:
+                    acc_grads[k].add_(grads[k])
         ms_loop, _ = timed(loop_step, max(3, args.steps // 2), 2)
         loop = {"views_per_s": V / (ms_loop / 1e3), "ms_per_step": ms_loop,
                 "speedup_batched_over_loop": ms_loop / ms_batched}
@@ -247,7 +254,7 @@ def run_ours(args, rank, world):
     ms_e2e = None if args.no_e2e else timed(e2e_step, max(3, args.steps // 2), 2)[0]
 
     # ---- roofline of the dominant kernel ----
-    roof = roofline(stages, args, needed, rz, clk)
+    roof, per_stage = roofline(stages, args, needed, rz, clk, V, rz.pixels)
 
     out = {
         "metric": METRIC, "value": V * world / (ms_batched / 1e3), "unit": "views/s", "n_gpus": world,
@@ -266,6 +273,7 @@ def run_ours(args, rank, world):
         "per_view_loop": loop,
         "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in (stages or {}).items() if v[1]},
         "roofline": roof,
+        "stage_roofline": per_stage,
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu:
@@ -283,51 +291,71 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def roofline(stages, args, needed, rz, clk):
-    """Achieved / peak for the stage with the largest time per step."""
-    if not stages:
-        return None
-    peaks, src = _peaks()
-    steps = args.steps
-    per_step = {k: v[0] / steps for k, v in stages.items() if v[1]}
-    dom = max(per_step, key=per_step.get)
-    ms_launch = stages[dom][0] / stages[dom][1]
+def stage_work(rz, needed, V, pixels):
+    """Algorithmic work of each stage for one step: (bound, amount, unit).
+    Bytes are what the stage must read and write in HBM (each array once);
+    FLOPs are counted on blended pairs only (see FWD_/BWD_FLOP_PER_BLENDED)."""
+    import torch
     R, K = needed
+    n = rz.n
     tiles = int(rz.layout.tiles)
     bits = max(1, int(np.ceil(np.log2(max(tiles, 2)))))
-    passes = (bits + 7) // 8
-    hbm = peaks.get("hbm_gbs", 6800.0)
+    passes = max(1, (bits + 7) // 8)
+    blended = rz.records()["pixel_stats"].to(torch.int64)[:, 1].sum().item()
+    return {
+        "count_visible": ("hbm", 44.0 * n + 4.0 * n + n * V, "B"),
+        "scan_records": ("hbm", 12.0 * n, "B"),
+        "preprocess": ("hbm", 236.0 * n + n * V + 8.0 * n + 76.0 * R, "B"),
+        "depth_sort": ("hbm", 4 * 16.0 * R, "B"),
+        "scan_tiles": ("hbm", 12.0 * R, "B"),
+        "tile_sort": ("hbm", 8.0 * K + passes * 16.0 * K - 4.0 * K, "B"),
+        "ranges": ("hbm", 8.0 * R + 24.0 * tiles, "B"),
+        "blend_forward": ("alu", FWD_FLOP_PER_BLENDED * blended, "FLOP"),
+        "zero_grads": ("hbm", 48.0 * R, "B"),
+        "blend_backward": ("alu", BWD_FLOP_PER_BLENDED * blended, "FLOP"),
+        "preprocess_backward": ("hbm", 472.0 * n + 124.0 * R, "B"),
+        "dssim": ("hbm", 44.0 * 3 * pixels, "B"),
+        "adc": ("hbm", 12.0 * R + 32.0 * n, "B"),
+    }, blended
+
+
+def roofline(stages, args, needed, rz, clk, V, pixels):
+    """Per-stage achieved / peak, and the dominant stage's entry."""
+    if not stages:
+        return None, None
     import torch
+    peaks, src = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    if dom == "tile_sort":
-        traffic = passes * 16.0 * K  # read (key, value), write (key, value) per pass
-        ach = traffic / (ms_launch / 1e3) / 1e9
-        return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "peak_source": src,
-                "algorithmic": f"{passes} passes x 16 B x {K} keys"}
-    if dom in ("blend_forward", "blend_backward"):
-        rec = rz.records()
-        stats = rec["pixel_stats"].to(torch.int64)
-        blended = stats[:, 1].sum().item()    # (pixel, Gaussian) pairs blended
+    mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1455.0)
+    alu_peak = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    work, blended = stage_work(rz, needed, V, pixels)
+    table = {}
+    for name, (ms_total, launches) in stages.items():
+        if not launches or name not in work:
+            continue
+        bound, amount, unit = work[name]
+        ms = ms_total / args.steps  # per step (a stage may launch several kernels)
+        if bound == "alu":
+            ach = amount / (ms / 1e3) / 1e12
+            table[name] = {"bound": "alu", "ms": round(ms, 4), "achieved": round(ach, 3), "peak": round(alu_peak, 2),
+                           "unit": "TFLOP/s", "frac": round(ach / alu_peak, 4)}
+        else:
+            ach = amount / (ms / 1e3) / 1e9
+            table[name] = {"bound": "hbm", "ms": round(ms, 4), "achieved": round(ach, 1), "peak": hbm,
+                           "unit": "GB/s", "frac": round(ach / hbm, 4)}
+    dom = max(table, key=lambda k: table[k]["ms"])
+    d = dict(table[dom])
+    d.pop("ms")
+    d["kernel"] = dom
+    d["traffic"] = None
+    if d["bound"] == "alu":
         per = FWD_FLOP_PER_BLENDED if dom == "blend_forward" else BWD_FLOP_PER_BLENDED
-        flops = per * blended
-        what = f"{per} FLOP x {blended} blended (pixel, Gaussian) pairs" 
-        mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1455.0)
-        peak = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-        ach = flops / (ms_launch / 1e3) / 1e12
-        return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)",
-                "algorithmic": what}
-    # other stages: bytes moved estimate
-    byte_est = {"preprocess": 236.0 * rz.n + 64.0 * R, "duplicate": 8.0 * K + 12.0 * R,
-                "depth_sort": 4 * 16.0 * R, "preprocess_backward": 236.0 * 2 * rz.n + 48.0 * R}
-    b = byte_est.get(dom)
-    if b is None:
-        return {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
-                "traffic": None}
-    ach = b / (ms_launch / 1e3) / 1e9
-    return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-            "traffic": None, "peak_source": src}
+        d["algorithmic"] = f"{per} FLOP x {blended} blended (pixel, Gaussian) pairs per launch"
+        d["peak_source"] = f"{sms} SMs x 128 FP32 lanes x 2 FLOP x {mhz:.0f} MHz (sampled SM clock)"
+    else:
+        d["peak_source"] = f"MEASURED_PEAKS.json hbm_gbs ({src})"
+    return d, table
 
 
 # ---------------------------------------------------------------------------
