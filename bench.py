@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-loop", action="store_true", help="skip the per-view launch loop")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) measurement")
+    ap.add_argument("--no-partial", action="store_true",
+                    help="skip the partial-rendering comparison (full / masked / thread-efficient)")
     return ap.parse_args()
 
 
@@ -238,6 +240,30 @@ def run_ours(args, rank, world):
         loop = {"views_per_s": V / (ms_loop / 1e3), "ms_per_step": ms_loop,
                 "speedup_batched_over_loop": ms_loop / ms_batched}
 
+    # ---- partial rendering (Sec. 5.1.1): one image's worth of pixels over the V views ----
+    partial = None
+    if not args.no_partial:
+        ss = rz.sample_set(V, seed=11)
+
+        def render_step(samples=None, masked=False):
+            rz.forward(sc, samples=samples, masked=masked)
+            rz.backward(sc, dimg, grads, samples=samples, masked=masked)
+
+        modes = {}
+        for name, kw in (("full", {}), ("masked_partial", {"samples": ss, "masked": True}),
+                         ("thread_efficient", {"samples": ss})):
+            ms_m, st_m = timed(lambda: render_step(**kw), max(3, args.steps // 2), 2, profile=True)
+            nst = max(3, args.steps // 2)
+            modes[name] = {"render_fwd_bwd_ms": round(ms_m, 4),
+                           "blend_forward_ms": round(st_m.get("blend_forward", (0, 0))[0] / nst, 4),
+                           "blend_backward_ms": round(st_m.get("blend_backward", (0, 0))[0] / nst, 4)}
+        partial = {"group": V, "sampled_pixels": int(ss.offsets[-1].item()), "pixels": rz.pixels,
+                   "modes": modes,
+                   "blend_speedup_thread_efficient_over_masked":
+                       (modes["masked_partial"]["blend_forward_ms"] + modes["masked_partial"]["blend_backward_ms"]) /
+                       max(1e-9, modes["thread_efficient"]["blend_forward_ms"] +
+                           modes["thread_efficient"]["blend_backward_ms"])}
+
     # ---- end to end through the C ABI with host buffers ----
     host = {k: v.cpu().pin_memory() for k, v in params.items()}
     host_tgt = tgt.cpu().pin_memory()
@@ -271,6 +297,7 @@ def run_ours(args, rank, world):
                                             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "per_view_loop": loop,
+        "partial_rendering": partial,
         "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in (stages or {}).items() if v[1]},
         "roofline": roof,
         "stage_roofline": per_stage,

@@ -15,6 +15,9 @@
  *                                gradients of all of them (Sec. 5.2).
  *   - mvgs_dssim_loss            photometric l1 + D-SSIM (Sec. 3 and the SSIM
  *                                equations of Sec. 5.1.2), per view.
+ *   - mvgs_render_views_sampled  thread-efficient partial rendering (Sec.
+ *                                5.1.1, Alg. 3): per (tile, view) only an
+ *                                index array of sampled pixels is blended.
  *   - mvgs_adc_accumulate        the multi-view densification error metrics
  *                                E_1 and E_2 of Sec. 5.2.2 (norm per pixel /
  *                                per view, then add).
@@ -97,7 +100,7 @@ typedef struct mvgs_scene {
 typedef struct mvgs_config {
     int32_t tile_w, tile_h;
     float bg[3];      /* background colour added with the final transmittance */
-    uint32_t flags;   /* reserved, must be 0 */
+    uint32_t flags;   /* 0, or MVGS_FLAG_MASKED_PARTIAL (sampled calls only) */
     int32_t pixels_per_thread;  /* blend lanes each own this many pixels of a
                                    tile column, so one warp blends a strip of
                                    tile_w columns by (32 / tile_w) *
@@ -105,6 +108,12 @@ typedef struct mvgs_config {
                                    1, 2, 4 or 8 with the strip height dividing
                                    tile_h.  Results do not depend on it. */
 } mvgs_config;
+
+/* cfg->flags bit for the sampled calls: blend whole strips and leave the
+ * lanes of unsampled pixels idle (the naive partial rendering of Fig. 3b),
+ * instead of packing the samples into runs (Alg. 3).  Same results; for
+ * comparison. */
+#define MVGS_FLAG_MASKED_PARTIAL 1u
 
 /* Capacities the caller sized `state` and `workspace` for:
  * records = visible (Gaussian, view) pairs, keys = (record, tile) pairs. */
@@ -174,6 +183,60 @@ mvgs_status mvgs_render_views_backward(const mvgs_scene* scene, const mvgs_camer
                                        size_t workspace_bytes, float* g_means, float* g_log_scales, float* g_quats,
                                        float* g_opacity_logits, float* g_sh, float* g_mean2d, float* e1,
                                        mvgs_stream stream);
+
+/* ---- thread-efficient partial rendering (Sec. 5.1.1, Alg. 3, Fig. 3c) ----
+ * Each (view, tile) renders only a sub-sample of its pixels, given as an
+ * index array per (tile, view): the blend packs the samples of a tile into
+ * runs of 32 * pixels_per_thread, one warp each, so no lane idles on an
+ * unsampled pixel.  The sort and the tile lists are those of the full render.
+ *
+ * A sample set, device arrays owned by the caller:
+ *   offsets [layout.tiles + 1] int64: the samples of global tile t (view-major
+ *           tile numbering, row-major tiles inside a view) are
+ *           pixels[offsets[t] .. offsets[t + 1]);
+ *   pixels  uint16 pixel index inside the tile, ly * tile_w + lx, at most
+ *           layout.pixels entries in all.  Indices outside the image or the
+ *           tile are skipped; a pixel listed twice is rendered twice. */
+typedef struct mvgs_samples {
+    const int64_t* offsets;
+    const uint16_t* pixels;
+} mvgs_samples;
+
+/* Scratch bytes for mvgs_partial_samples. */
+size_t mvgs_partial_samples_workspace_size(const mvgs_camera* cams, int32_t V, const mvgs_config* cfg);
+
+/* Fills a sample set: view v renders pixel (x, y) when
+ *   floor(group * (h >> 32) / 2^32) == v mod group,
+ * h = SplitMix64 output number 2^32 y + x + 1 of the stream seeded with
+ * `seed`.  So `group` consecutive views of one resolution split every pixel
+ * position between them exactly once (one image's worth of pixels over
+ * `group` views), each taking about 1/group of its pixels.  The paper leaves
+ * the sub-sampling rule open; this one is seeded and reproducible.
+ *   offsets [layout.tiles + 1], pixels [layout.pixels]: device, written.
+ * group >= 1; the tile size in cfg must be the one used to render. */
+mvgs_status mvgs_partial_samples(const mvgs_camera* cams, int32_t V, const mvgs_config* cfg, int32_t group,
+                                 uint64_t seed, int64_t* offsets, uint16_t* pixels, void* workspace,
+                                 size_t workspace_bytes, mvgs_stream stream);
+
+/* mvgs_render_views restricted to a sample set: writes the images,
+ * final_T, n_contrib and pixel_stats of the sampled pixels only (every other
+ * pixel of `images` and of those state arrays is left as it was).  A sampled
+ * pixel gets exactly the value the full render gives it. */
+mvgs_status mvgs_render_views_sampled(const mvgs_scene* scene, const mvgs_camera* cams, int32_t V,
+                                      const mvgs_config* cfg, const mvgs_capacity* cap, const mvgs_samples* samples,
+                                      float* images, void* state, size_t state_bytes, void* workspace,
+                                      size_t workspace_bytes, mvgs_capacity* needed, mvgs_stream stream);
+
+/* Backward of mvgs_render_views_sampled (same sample set): only the sampled
+ * pixels of dL_dimages are read; equals the full backward with dL_dimages
+ * zero at every unsampled pixel. */
+mvgs_status mvgs_render_views_sampled_backward(const mvgs_scene* scene, const mvgs_camera* cams, int32_t V,
+                                               const mvgs_config* cfg, const mvgs_capacity* cap,
+                                               const mvgs_samples* samples, const float* dL_dimages,
+                                               const void* state, size_t state_bytes, void* workspace,
+                                               size_t workspace_bytes, float* g_means, float* g_log_scales,
+                                               float* g_quats, float* g_opacity_logits, float* g_sh,
+                                               float* g_mean2d, float* e1, mvgs_stream stream);
 
 /* Scratch bytes mvgs_dssim_loss needs for these views (hw: host [V, 2] of
  * (height, width)). */

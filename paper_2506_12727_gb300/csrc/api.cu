@@ -128,6 +128,10 @@ struct Plan {
     size_t w_cams = 0, w_counts = 0, w_vis = 0, w_scan = 0, w_dkeys_a = 0, w_dkeys_b = 0, w_ids_a = 0, w_ids_b = 0,
            w_order = 0, w_tiles = 0, w_tile_off = 0, w_keys_a = 0, w_keys_b = 0, w_vals_a = 0, w_vals_b = 0,
            w_radix = 0, w_tcount = 0, w_torder = 0, w_counter = 0;
+    // workspace offsets of the sampled blend (forward and backward each carve their own)
+    size_t w_chunk_off = 0, w_chunk_map = 0, w_chunk_tmp = 0, w_mask = 0;
+    size_t b_chunk_off = 0, b_chunk_map = 0, b_chunk_tmp = 0, b_mask = 0;
+    long long chunk_cap = 0;
     // workspace offsets (backward)
     size_t b_cams = 0, b_grad = 0, b_counter = 0;
 };
@@ -137,7 +141,7 @@ mvgs_status check_config(const mvgs_config* cfg) {
     const int tw = cfg->tile_w, th = cfg->tile_h;
     const bool side_ok = (tw == 8 || tw == 16 || tw == 32) && (th == 8 || th == 16 || th == 32 || th == 64);
     if (!side_ok) return fail(MVGS_EINVAL, "unsupported tile %dx%d (width 8, 16 or 32; height 8 to 64)", tw, th);
-    if (cfg->flags != 0) return fail(MVGS_EINVAL, "flags must be 0");
+    if (cfg->flags & ~(uint32_t)MVGS_FLAG_MASKED_PARTIAL) return fail(MVGS_EINVAL, "unknown flags 0x%x", cfg->flags);
     const int ppt = cfg->pixels_per_thread;
     if (ppt != 0) {
         // a warp covers tile_w columns and (32 / tile_w) * ppt rows of a tile
@@ -237,11 +241,21 @@ mvgs_status make_plan(long long n, const mvgs_camera* cams, int V, const mvgs_co
     P.w_tcount = w.take(tile_count_temp_bytes(P.cams.data(), V, tiles));
     P.w_torder = w.take(tile_order_temp_bytes(tiles));
     P.w_counter = w.take(sizeof(int));
+    // runs of at least 32 samples: at most one partial run per tile
+    P.chunk_cap = tiles + pixels / 32 + 1;
+    P.w_chunk_off = w.take((size_t)(tiles + 1) * sizeof(long long));
+    P.w_chunk_map = w.take((size_t)P.chunk_cap * sizeof(int));
+    P.w_chunk_tmp = w.take(chunk_temp_bytes(tiles));
+    P.w_mask = w.take((size_t)pixels);
     const size_t fwd_bytes = w.off;
     Carver b;
     P.b_cams = b.take((size_t)V * sizeof(DevCam));
     P.b_grad = b.take(R * kGradStride * sizeof(float));
     P.b_counter = b.take(sizeof(int));
+    P.b_chunk_off = b.take((size_t)(tiles + 1) * sizeof(long long));
+    P.b_chunk_map = b.take((size_t)P.chunk_cap * sizeof(int));
+    P.b_chunk_tmp = b.take(chunk_temp_bytes(tiles));
+    P.b_mask = b.take((size_t)pixels);
     L.workspace_bytes = fwd_bytes > b.off ? fwd_bytes : b.off;
     return MVGS_OK;
 }
@@ -304,6 +318,40 @@ int bits_for(long long tiles) {
     return b;
 }
 
+// Points the blend at a sample set: sampled runs (Alg. 3) or, with the
+// masked-partial flag, the full strips with unsampled pixels idle (Fig. 3b).
+void attach_samples(BlendArgs& ba, const mvgs_samples* smp, const mvgs_config* cfg, const Plan& P, void* ws,
+                    size_t off_chunk, size_t off_map, size_t off_tmp, size_t off_mask, cudaStream_t s) {
+    ba.s_off = nullptr;
+    ba.s_pix = nullptr;
+    ba.chunk_off = nullptr;
+    ba.chunk_map = nullptr;
+    ba.chunk_cap = 0;
+    ba.pixel_mask = nullptr;
+    if (!smp) return;
+    const long long* s_off = reinterpret_cast<const long long*>(smp->offsets);
+    if (cfg->flags & MVGS_FLAG_MASKED_PARTIAL) {
+        uint8_t* mask = at<uint8_t>(ws, off_mask);
+        launch_samples_to_mask(ba.cams, ba.V, P.tiles, P.pixels, ba.tw, ba.th, s_off, smp->pixels, mask, s);
+        ba.pixel_mask = mask;
+        return;
+    }
+    long long* chunk_off = at<long long>(ws, off_chunk);
+    int* chunk_map = at<int>(ws, off_map);
+    launch_sample_chunks(ba.order, s_off, P.tiles, 32 * ba.ppt, chunk_off, chunk_map, P.chunk_cap,
+                         at<void>(ws, off_tmp), s);
+    ba.s_off = s_off;
+    ba.s_pix = smp->pixels;
+    ba.chunk_off = chunk_off;
+    ba.chunk_map = chunk_map;
+    ba.chunk_cap = P.chunk_cap;
+}
+
+mvgs_status check_samples(const mvgs_samples* smp) {
+    if (smp && (!smp->offsets || !smp->pixels)) return fail(MVGS_EINVAL, "sample set with a NULL array");
+    return MVGS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -359,11 +407,13 @@ mvgs_status mvgs_render_layout(int64_t n, const mvgs_camera* cams, int32_t V, co
     return MVGS_OK;
 }
 
-mvgs_status mvgs_render_views(const mvgs_scene* scene, const mvgs_camera* cams, int32_t V, const mvgs_config* cfg,
-                              const mvgs_capacity* cap, float* images, void* state, size_t state_bytes,
-                              void* workspace, size_t workspace_bytes, mvgs_capacity* needed, mvgs_stream stream) {
+static mvgs_status render_impl(const mvgs_scene* scene, const mvgs_camera* cams, int32_t V, const mvgs_config* cfg,
+                               const mvgs_capacity* cap, float* images, void* state, size_t state_bytes,
+                               void* workspace, size_t workspace_bytes, mvgs_capacity* needed,
+                               const mvgs_samples* smp, mvgs_stream stream) {
     mvgs_status st = check_scene(scene);
     if (st != MVGS_OK) return st;
+    if ((st = check_samples(smp)) != MVGS_OK) return st;
     Plan P;
     st = make_plan(scene->n, cams, V, cfg, cap, P);
     if (st != MVGS_OK) return st;
@@ -470,20 +520,22 @@ mvgs_status mvgs_render_views(const mvgs_scene* scene, const mvgs_camera* cams, 
     for (int i = 0; i < 3; i++) ba.bg[i] = cfg->bg[i];
     {
         StageTimer t(MVGS_STAGE_BLEND_FORWARD, s);
+        attach_samples(ba, smp, cfg, P, workspace, P.w_chunk_off, P.w_chunk_map, P.w_chunk_tmp, P.w_mask, s);
         launch_blend_forward(ba, at<int>(workspace, P.w_counter), images, at<float>(state, L.off_final_T),
                              at<uint32_t>(state, L.off_n_contrib), at<uint2>(state, L.off_pixel_stats), s);
     }
     return cuda_check("render");
 }
 
-mvgs_status mvgs_render_views_backward(const mvgs_scene* scene, const mvgs_camera* cams, int32_t V,
-                                       const mvgs_config* cfg, const mvgs_capacity* cap, const float* dL_dimages,
-                                       const void* state, size_t state_bytes, void* workspace,
-                                       size_t workspace_bytes, float* g_means, float* g_log_scales, float* g_quats,
-                                       float* g_opacity_logits, float* g_sh, float* g_mean2d, float* e1,
-                                       mvgs_stream stream) {
+static mvgs_status backward_impl(const mvgs_scene* scene, const mvgs_camera* cams, int32_t V,
+                                 const mvgs_config* cfg, const mvgs_capacity* cap, const float* dL_dimages,
+                                 const void* state, size_t state_bytes, void* workspace, size_t workspace_bytes,
+                                 float* g_means, float* g_log_scales, float* g_quats, float* g_opacity_logits,
+                                 float* g_sh, float* g_mean2d, float* e1, const mvgs_samples* smp,
+                                 mvgs_stream stream) {
     mvgs_status st = check_scene(scene);
     if (st != MVGS_OK) return st;
+    if ((st = check_samples(smp)) != MVGS_OK) return st;
     Plan P;
     st = make_plan(scene->n, cams, V, cfg, cap, P);
     if (st != MVGS_OK) return st;
@@ -523,6 +575,7 @@ mvgs_status mvgs_render_views_backward(const mvgs_scene* scene, const mvgs_camer
     for (int i = 0; i < 3; i++) ba.bg[i] = cfg->bg[i];
     {
         StageTimer t(MVGS_STAGE_BLEND_BACKWARD, s);
+        attach_samples(ba, smp, cfg, P, workspace, P.b_chunk_off, P.b_chunk_map, P.b_chunk_tmp, P.b_mask, s);
         launch_blend_backward(ba, at<int>(workspace, P.b_counter), dL_dimages, at<float>(state, L.off_final_T),
                               at<uint32_t>(state, L.off_n_contrib), rec_grad, s);
     }
@@ -532,6 +585,73 @@ mvgs_status mvgs_render_views_backward(const mvgs_scene* scene, const mvgs_camer
                                    g_opacity_logits, g_sh, g_mean2d, e1, s);
     }
     return cuda_check("render backward");
+}
+
+mvgs_status mvgs_render_views(const mvgs_scene* scene, const mvgs_camera* cams, int32_t V, const mvgs_config* cfg,
+                              const mvgs_capacity* cap, float* images, void* state, size_t state_bytes,
+                              void* workspace, size_t workspace_bytes, mvgs_capacity* needed, mvgs_stream stream) {
+    return render_impl(scene, cams, V, cfg, cap, images, state, state_bytes, workspace, workspace_bytes, needed,
+                       nullptr, stream);
+}
+
+mvgs_status mvgs_render_views_backward(const mvgs_scene* scene, const mvgs_camera* cams, int32_t V,
+                                       const mvgs_config* cfg, const mvgs_capacity* cap, const float* dL_dimages,
+                                       const void* state, size_t state_bytes, void* workspace,
+                                       size_t workspace_bytes, float* g_means, float* g_log_scales, float* g_quats,
+                                       float* g_opacity_logits, float* g_sh, float* g_mean2d, float* e1,
+                                       mvgs_stream stream) {
+    return backward_impl(scene, cams, V, cfg, cap, dL_dimages, state, state_bytes, workspace, workspace_bytes,
+                         g_means, g_log_scales, g_quats, g_opacity_logits, g_sh, g_mean2d, e1, nullptr, stream);
+}
+
+mvgs_status mvgs_render_views_sampled(const mvgs_scene* scene, const mvgs_camera* cams, int32_t V,
+                                      const mvgs_config* cfg, const mvgs_capacity* cap, const mvgs_samples* samples,
+                                      float* images, void* state, size_t state_bytes, void* workspace,
+                                      size_t workspace_bytes, mvgs_capacity* needed, mvgs_stream stream) {
+    if (!samples) return fail(MVGS_EINVAL, "samples is NULL");
+    return render_impl(scene, cams, V, cfg, cap, images, state, state_bytes, workspace, workspace_bytes, needed,
+                       samples, stream);
+}
+
+mvgs_status mvgs_render_views_sampled_backward(const mvgs_scene* scene, const mvgs_camera* cams, int32_t V,
+                                               const mvgs_config* cfg, const mvgs_capacity* cap,
+                                               const mvgs_samples* samples, const float* dL_dimages,
+                                               const void* state, size_t state_bytes, void* workspace,
+                                               size_t workspace_bytes, float* g_means, float* g_log_scales,
+                                               float* g_quats, float* g_opacity_logits, float* g_sh,
+                                               float* g_mean2d, float* e1, mvgs_stream stream) {
+    if (!samples) return fail(MVGS_EINVAL, "samples is NULL");
+    return backward_impl(scene, cams, V, cfg, cap, dL_dimages, state, state_bytes, workspace, workspace_bytes,
+                         g_means, g_log_scales, g_quats, g_opacity_logits, g_sh, g_mean2d, e1, samples, stream);
+}
+
+size_t mvgs_partial_samples_workspace_size(const mvgs_camera* cams, int32_t V, const mvgs_config* cfg) {
+    Plan P;
+    const mvgs_capacity cap{0, 0};
+    if (make_plan(0, cams, V, cfg, &cap, P) != MVGS_OK) return 0;
+    return 256 + ((size_t)V * sizeof(DevCam) + 255) / 256 * 256 + sample_temp_bytes(P.tiles);
+}
+
+mvgs_status mvgs_partial_samples(const mvgs_camera* cams, int32_t V, const mvgs_config* cfg, int32_t group,
+                                 uint64_t seed, int64_t* offsets, uint16_t* pixels, void* workspace,
+                                 size_t workspace_bytes, mvgs_stream stream) {
+    Plan P;
+    const mvgs_capacity cap{0, 0};
+    mvgs_status st = make_plan(0, cams, V, cfg, &cap, P);
+    if (st != MVGS_OK) return st;
+    if (group < 1) return fail(MVGS_EINVAL, "group must be >= 1");
+    if (!offsets || !pixels || !workspace) return fail(MVGS_EINVAL, "NULL offsets, pixels or workspace");
+    const size_t cam_bytes = ((size_t)V * sizeof(DevCam) + 255) / 256 * 256;
+    const size_t need = 256 + cam_bytes + sample_temp_bytes(P.tiles);
+    if (workspace_bytes < need) return fail(MVGS_ENOSPACE, "workspace %zu < %zu bytes", workspace_bytes, need);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // 256-byte aligned pieces of the caller's workspace
+    char* base = reinterpret_cast<char*>(((uintptr_t)workspace + 255) / 256 * 256);
+    DevCam* dcams = reinterpret_cast<DevCam*>(base);
+    upload_cams(P.cams.data(), V, dcams, s);
+    launch_partial_samples(dcams, V, P.tiles, cfg->tile_w, cfg->tile_h, group, (unsigned long long)seed,
+                           reinterpret_cast<long long*>(offsets), pixels, base + cam_bytes, s);
+    return cuda_check("partial samples");
 }
 
 size_t mvgs_dssim_workspace_size(const int32_t* hw, int32_t V) {

@@ -38,46 +38,126 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int WBATCH = 128;         // Gaussians per warp batch in shared memory
 constexpr int WARPS_PER_BLOCK = 4;
 
-// One warp's work item: a strip of a tile.
-struct Strip {
-    long long gt;          // global (view, tile) id, -1 when the queue is empty
+// One warp's work item: PPT pixels per lane of one (view, tile) pair -- a
+// strip of the tile, or (sampled mode) a run of 32 * PPT of the tile's pixel
+// samples.
+template <int PPT>
+struct Work {
+    long long gt;               // global (view, tile) id, -1 when the queue is empty
     const DevCam* cam;
-    int px;                // this lane's column
-    int py0, step;         // this lane's first row and the distance between its rows
-    float sx0, sx1, sy0, sy1;  // pixel-centre bounds of the strip inside the image
+    float fx[PPT], fy[PPT];     // pixel centres (strips: one column, fx[k] all equal)
+    int pix[PPT];               // pixel index in the view (y W + x); -1 for an idle slot
+    float sx0, sx1, sy0, sy1;   // bounds of the warp's pixel centres
 };
 
-// Takes the next strip for the warp (lane 0 takes it, all lanes get it).
-__device__ __forceinline__ Strip next_strip(const BlendArgs& a, int* counter, int lane) {
+__device__ __forceinline__ int take_item(int* counter, int lane) {
     int item = 0;
     if (lane == 0) item = atomicAdd(counter, 1);
-    item = __shfl_sync(kFull, item, 0);
-    Strip s;
-    const long long total = a.tiles * a.strips;
-    if (item >= total) {
-        s.gt = -1;
-        return s;
-    }
-    s.gt = (long long)a.order[item / a.strips];
-    const int strip = item % a.strips;
-    int v = 0;
-    if (lane == 0) v = find_view(a.cams, a.V, s.gt);
-    v = __shfl_sync(kFull, v, 0);
-    s.cam = &a.cams[v];
-    const long long local = s.gt - s.cam->tile_base;
-    const int tx = (int)(local % s.cam->tiles_x), ty = (int)(local / s.cam->tiles_x);
-    s.step = 32 / a.tw;  // thread rows of the warp
-    s.px = tx * a.tw + lane % a.tw;
-    s.py0 = ty * a.th + strip * a.strip_h + lane / a.tw;
-    const int x0 = tx * a.tw, y0 = ty * a.th + strip * a.strip_h;
-    s.sx0 = x0 + 0.5f;
-    s.sx1 = (float)min(x0 + a.tw, s.cam->W) - 0.5f;
-    s.sy0 = y0 + 0.5f;
-    s.sy1 = (float)min(y0 + a.strip_h, s.cam->H) - 0.5f;
-    return s;
+    return __shfl_sync(kFull, item, 0);
 }
 
+__device__ __forceinline__ const DevCam* view_of(const BlendArgs& a, long long gt, int lane) {
+    int v = 0;
+    if (lane == 0) v = find_view(a.cams, a.V, gt);
+    v = __shfl_sync(kFull, v, 0);
+    return &a.cams[v];
+}
+
+// Next strip for the warp.  With a pixel mask (the naive partial rendering
+// of Fig. 3b) masked pixels are idle slots of their lanes.
 template <int PPT>
+__device__ __forceinline__ bool next_strip(const BlendArgs& a, int* counter, int lane, Work<PPT>& w) {
+    const int item = take_item(counter, lane);
+    if ((long long)item >= a.tiles * a.strips) return false;
+    w.gt = (long long)a.order[item / a.strips];
+    const int strip = item % a.strips;
+    w.cam = view_of(a, w.gt, lane);
+    const DevCam& cam = *w.cam;
+    const long long local = w.gt - cam.tile_base;
+    const int tx = (int)(local % cam.tiles_x), ty = (int)(local / cam.tiles_x);
+    const int step = 32 / a.tw;  // thread rows of the warp
+    const int px = tx * a.tw + lane % a.tw;
+    const int x0 = tx * a.tw, y0 = ty * a.th + strip * a.strip_h;
+    const int py0 = y0 + lane / a.tw;
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        const int py = py0 + k * step;
+        w.fx[k] = px + 0.5f;
+        w.fy[k] = py + 0.5f;
+        int p = -1;
+        if (px < cam.W && py < cam.H) {
+            p = py * cam.W + px;
+            if (a.pixel_mask && !a.pixel_mask[cam.pix_base + p]) p = -1;
+        }
+        w.pix[k] = p;
+    }
+    w.sx0 = x0 + 0.5f;
+    w.sx1 = (float)min(x0 + a.tw, cam.W) - 0.5f;
+    w.sy0 = y0 + 0.5f;
+    w.sy1 = (float)min(y0 + a.strip_h, cam.H) - 0.5f;
+    return true;
+}
+
+// Next run of pixel samples (Alg. 3): lanes take consecutive samples of the
+// tile's list, so every lane of the warp has a pixel to blend except in the
+// tile's last run.  Runs whose samples are all invalid are skipped.
+template <int PPT>
+__device__ __forceinline__ bool next_samples(const BlendArgs& a, int* counter, int lane, long long total,
+                                             Work<PPT>& w) {
+    for (;;) {
+        const int item = take_item(counter, lane);
+        if ((long long)item >= total) return false;
+        const int i = a.chunk_map[item];
+        w.gt = (long long)a.order[i];
+        const long long chunk = (long long)item - a.chunk_off[i];
+        w.cam = view_of(a, w.gt, lane);
+        const DevCam& cam = *w.cam;
+        const long long local = w.gt - cam.tile_base;
+        const int tx = (int)(local % cam.tiles_x), ty = (int)(local / cam.tiles_x);
+        const long long s0 = a.s_off[w.gt] + chunk * 32 * PPT, s1 = a.s_off[w.gt + 1];
+        int xmin = 0x7fffffff, ymin = 0x7fffffff, xmax = -1, ymax = -1;
+#pragma unroll
+        for (int k = 0; k < PPT; k++) {
+            const long long si = s0 + k * 32 + lane;
+            int p = -1, px = 0, py = 0;
+            if (si < s1) {
+                const int li = a.s_pix[si];
+                const int lx = li % a.tw, ly = li / a.tw;
+                px = tx * a.tw + lx;
+                py = ty * a.th + ly;
+                if (ly < a.th && px < cam.W && py < cam.H) {
+                    p = py * cam.W + px;
+                    xmin = min(xmin, px);
+                    xmax = max(xmax, px);
+                    ymin = min(ymin, py);
+                    ymax = max(ymax, py);
+                }
+            }
+            w.fx[k] = px + 0.5f;
+            w.fy[k] = py + 0.5f;
+            w.pix[k] = p;
+        }
+        xmax = __reduce_max_sync(kFull, xmax);
+        if (xmax < 0) continue;  // no valid sample in this run
+        xmin = __reduce_min_sync(kFull, xmin);
+        ymin = __reduce_min_sync(kFull, ymin);
+        ymax = __reduce_max_sync(kFull, ymax);
+        w.sx0 = xmin + 0.5f;
+        w.sx1 = xmax + 0.5f;
+        w.sy0 = ymin + 0.5f;
+        w.sy1 = ymax + 0.5f;
+        return true;
+    }
+}
+
+template <int PPT, bool SAMPLED>
+__device__ __forceinline__ bool next_work(const BlendArgs& a, int* counter, int lane, long long total,
+                                          Work<PPT>& w) {
+    if constexpr (SAMPLED) return next_samples<PPT>(a, counter, lane, total, w);
+    else return next_strip<PPT>(a, counter, lane, w);
+}
+
+template <int PPT, bool SAMPLED>
 __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(BlendArgs a, int* __restrict__ counter,
                                                                              float* __restrict__ img,
                                                                              float* __restrict__ final_T,
@@ -94,29 +174,26 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(Ble
     float4* wrgb = s_rgb[w];
     uint32_t* wpos = s_pos[w];
     constexpr uint32_t ALL = (1u << PPT) - 1u;
-    for (;;) {
-        const Strip st = next_strip(a, counter, lane);
-        if (st.gt < 0) break;
+    const long long total = SAMPLED ? min(a.chunk_off[a.tiles], a.chunk_cap) : 0;
+    Work<PPT> st;
+    while (next_work<PPT, SAMPLED>(a, counter, lane, total, st)) {
         const DevCam& cam = *st.cam;
-        const float fx = st.px + 0.5f;
         const long long start = a.ranges[2 * st.gt], end = a.ranges[2 * st.gt + 1];
-        float fy[PPT], T[PPT], C0[PPT], C1[PPT], C2[PPT];
+        float T[PPT], C0[PPT], C1[PPT], C2[PPT];
         uint32_t last[PPT], stop[PPT], nblend[PPT];
         uint32_t done = 0;
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
-            const int py = st.py0 + k * st.step;
-            fy[k] = py + 0.5f;
             T[k] = 1.f;
             C0[k] = C1[k] = C2[k] = 0.f;
             last[k] = 0;
             stop[k] = (uint32_t)(end - start);  // list position where the pixel stopped
             nblend[k] = 0;
-            if (!(st.px < cam.W && py < cam.H)) done |= 1u << k;
+            if (st.pix[k] < 0) done |= 1u << k;
         }
         for (long long b = start; b < end; b += WBATCH) {
             if (__all_sync(kFull, done == ALL)) break;
-            // stage the Gaussians of this batch that can reach a pixel of the strip
+            // stage the Gaussians of this batch that can reach a pixel of the work item
             __syncwarp();
             int n = 0;
             for (int i0 = 0; i0 < WBATCH; i0 += 32) {
@@ -145,25 +222,26 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(Ble
             for (int j = 0; j < n; j++) {
                 const float2 m = wxy[j];
                 const float4 cr = wrgb[j];
-                const float dx = fx - m.x;
-                if (fabsf(dx) > cr.w) continue;  // outside the support for the whole column
+                const float dx0 = st.fx[0] - m.x;
+                if (!SAMPLED && fabsf(dx0) > cr.w) continue;  // outside the support for the whole column
                 const float4 co = wco[j];
                 const uint32_t pos = wpos[j];
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
                     if ((done >> k) & 1u) continue;
+                    const float dx = SAMPLED ? st.fx[k] - m.x : dx0;
                     float alpha, G, ax, ay;
-                    if (!pair_eval(dx, fy[k] - m.y, co, cr.w, alpha, G, ax, ay)) continue;
-                    const float Tn = T[k] * (1.f - alpha);
+                    if (!pair_eval(dx, st.fy[k] - m.y, co, cr.w, alpha, G, ax, ay)) continue;
+                    const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
                     if (Tn < kTMin) {
                         done |= 1u << k;
                         stop[k] = pos + 1;
                         continue;
                     }
-                    const float wgt = alpha * T[k];
-                    C0[k] += cr.x * wgt;
-                    C1[k] += cr.y * wgt;
-                    C2[k] += cr.z * wgt;
+                    const float wgt = __fmul_rn(alpha, T[k]);
+                    C0[k] = __fmaf_rn(cr.x, wgt, C0[k]);
+                    C1[k] = __fmaf_rn(cr.y, wgt, C1[k]);
+                    C2[k] = __fmaf_rn(cr.z, wgt, C2[k]);
                     T[k] = Tn;
                     last[k] = pos + 1;
                     nblend[k]++;
@@ -175,12 +253,11 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(Ble
         float* out = img + 3 * cam.pix_base;
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
-            const int py = st.py0 + k * st.step;
-            if (st.px < cam.W && py < cam.H) {
-                const long long p = (long long)py * cam.W + st.px;
-                out[p] = C0[k] + T[k] * a.bg[0];
-                out[HW + p] = C1[k] + T[k] * a.bg[1];
-                out[2 * HW + p] = C2[k] + T[k] * a.bg[2];
+            const long long p = st.pix[k];
+            if (p >= 0) {
+                out[p] = __fmaf_rn(T[k], a.bg[0], C0[k]);
+                out[HW + p] = __fmaf_rn(T[k], a.bg[1], C1[k]);
+                out[2 * HW + p] = __fmaf_rn(T[k], a.bg[2], C2[k]);
                 final_T[cam.pix_base + p] = T[k];
                 n_contrib[cam.pix_base + p] = last[k];
                 pixel_stats[cam.pix_base + p] = make_uint2(stop[k], nblend[k]);
@@ -206,7 +283,7 @@ __device__ __forceinline__ float warp_reduce_scatter16(float (&g)[16], int lane)
     return g[0] + __shfl_xor_sync(kFull, g[0], 1);
 }
 
-template <int PPT>
+template <int PPT, bool SAMPLED>
 __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(BlendArgs a, int* __restrict__ counter,
                                                                               const float* __restrict__ dimg,
                                                                               const float* __restrict__ final_T,
@@ -227,27 +304,24 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(Bl
     // value this lane adds after the reduce-scatter (lane pairs share one)
     const int my_val = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
     const bool adder = (lane & 1) == 0 && my_val < 10;
-    for (;;) {
-        const Strip st = next_strip(a, counter, lane);
-        if (st.gt < 0) break;
+    const long long total = SAMPLED ? min(a.chunk_off[a.tiles], a.chunk_cap) : 0;
+    Work<PPT> st;
+    while (next_work<PPT, SAMPLED>(a, counter, lane, total, st)) {
         const DevCam& cam = *st.cam;
-        const float fx = st.px + 0.5f;
         const long long HW = (long long)cam.W * cam.H;
         const float* din = dimg + 3 * cam.pix_base;
         // per pixel: T in front of the current Gaussian, dL/dC, and
         // U = dL/dC . (colour blended behind the current Gaussian + T_final bg)
-        float fy[PPT], T[PPT], d0[PPT], d1[PPT], d2[PPT], U[PPT];
+        float T[PPT], d0[PPT], d1[PPT], d2[PPT], U[PPT];
         uint32_t last[PPT];
         uint32_t mylast = 0;
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
-            const int py = st.py0 + k * st.step;
-            fy[k] = py + 0.5f;
             T[k] = 1.f;
             d0[k] = d1[k] = d2[k] = 0.f;
             last[k] = 0;
-            if (st.px < cam.W && py < cam.H) {
-                const long long p = (long long)py * cam.W + st.px;
+            const long long p = st.pix[k];
+            if (p >= 0) {
                 d0[k] = din[p];
                 d1[k] = din[HW + p];
                 d2[k] = din[2 * HW + p];
@@ -260,7 +334,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(Bl
         const uint32_t maxlast = __reduce_max_sync(kFull, mylast);
         const long long start = a.ranges[2 * st.gt];
         for (uint32_t b = 0; b < maxlast; b += WBATCH) {
-            // stage, back to front, the Gaussians that can reach the strip
+            // stage, back to front, the Gaussians that can reach the work item
             __syncwarp();
             int n = 0;
             for (int i0 = 0; i0 < WBATCH; i0 += 32) {
@@ -296,13 +370,14 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(Bl
                 bool any = false;
                 const float2 m = wxy[j];
                 const float4 cr = wrgb[j];
-                const float dx = fx - m.x;
-                if (pos < mylast && fabsf(dx) <= cr.w) {
+                const float dx0 = st.fx[0] - m.x;
+                if (pos < mylast && (SAMPLED || fabsf(dx0) <= cr.w)) {
                     const float4 co = wco[j];
 #pragma unroll
                     for (int k = 0; k < PPT; k++) {
                         if (pos >= last[k]) continue;
-                        const float dy = fy[k] - m.y;
+                        const float dx = SAMPLED ? st.fx[k] - m.x : dx0;
+                        const float dy = st.fy[k] - m.y;
                         float alpha, G, ax, ay;
                         if (!pair_eval(dx, dy, co, cr.w, alpha, G, ax, ay)) continue;
                         any = true;
@@ -374,16 +449,21 @@ void launch_blend_forward(const BlendArgs& a, int* counter, float* img, float* f
                           uint2* pixel_stats, cudaStream_t s) {
     if (a.tiles == 0) return;
     cudaMemsetAsync(counter, 0, sizeof(int), s);
-    const long long items = a.tiles * a.strips;
-#define MVGS_BF(P)                                                                                               \
-    blend_forward_kernel<P><<<grid_for(blend_forward_kernel<P>, items), 32 * WARPS_PER_BLOCK, 0, s>>>(          \
+    const bool sampled = a.s_off != nullptr;
+    // sampled mode: the number of runs is only known on the device; launch a
+    // full persistent grid
+    const long long items = sampled ? (1LL << 40) : a.tiles * a.strips;
+#define MVGS_BF(P, S)                                                                                            \
+    blend_forward_kernel<P, S><<<grid_for(blend_forward_kernel<P, S>, items), 32 * WARPS_PER_BLOCK, 0, s>>>(    \
         a, counter, img, final_T, n_contrib, pixel_stats)
+#define MVGS_BF2(P) if (sampled) MVGS_BF(P, true); else MVGS_BF(P, false)
     switch (a.ppt) {
-        case 1: MVGS_BF(1); break;
-        case 2: MVGS_BF(2); break;
-        case 8: MVGS_BF(8); break;
-        default: MVGS_BF(4); break;
+        case 1: MVGS_BF2(1); break;
+        case 2: MVGS_BF2(2); break;
+        case 8: MVGS_BF2(8); break;
+        default: MVGS_BF2(4); break;
     }
+#undef MVGS_BF2
 #undef MVGS_BF
     note_launches(1);
 }
@@ -392,16 +472,19 @@ void launch_blend_backward(const BlendArgs& a, int* counter, const float* dimg, 
                            const uint32_t* n_contrib, float* rec_grad, cudaStream_t s) {
     if (a.tiles == 0) return;
     cudaMemsetAsync(counter, 0, sizeof(int), s);
-    const long long items = a.tiles * a.strips;
-#define MVGS_BB(P)                                                                                               \
-    blend_backward_kernel<P><<<grid_for(blend_backward_kernel<P>, items), 32 * WARPS_PER_BLOCK, 0, s>>>(        \
+    const bool sampled = a.s_off != nullptr;
+    const long long items = sampled ? (1LL << 40) : a.tiles * a.strips;
+#define MVGS_BB(P, S)                                                                                            \
+    blend_backward_kernel<P, S><<<grid_for(blend_backward_kernel<P, S>, items), 32 * WARPS_PER_BLOCK, 0, s>>>(  \
         a, counter, dimg, final_T, n_contrib, rec_grad)
+#define MVGS_BB2(P) if (sampled) MVGS_BB(P, true); else MVGS_BB(P, false)
     switch (a.ppt) {
-        case 1: MVGS_BB(1); break;
-        case 2: MVGS_BB(2); break;
-        case 8: MVGS_BB(8); break;
-        default: MVGS_BB(4); break;
+        case 1: MVGS_BB2(1); break;
+        case 2: MVGS_BB2(2); break;
+        case 8: MVGS_BB2(8); break;
+        default: MVGS_BB2(4); break;
     }
+#undef MVGS_BB2
 #undef MVGS_BB
     note_launches(1);
 }

@@ -63,12 +63,15 @@ __device__ __forceinline__ int find_view(const DevCam* cams, int V, long long gt
 // unconditionally; the return value says whether the Gaussian takes part at
 // this pixel, and alpha, G = exp(power) and (ax, ay) are valid when it does.
 // The forward and the backward call this same function, so both take the
-// same decision for every pair.
+// same decision for every pair.  The products and fused multiply-adds are
+// spelled out (no contraction left to the compiler), so every kernel that
+// inlines it -- strips, sample runs, any pixels per lane -- rounds a pair the
+// same way.
 __device__ __forceinline__ bool pair_eval(float dx, float dy, float4 co, float radius, float& alpha, float& G,
                                           float& ax, float& ay) {
-    ax = co.x * dx + co.y * dy;
-    ay = co.y * dx + co.z * dy;
-    const float power = -0.5f * (dx * ax + dy * ay);
+    ax = __fmaf_rn(co.y, dy, __fmul_rn(co.x, dx));
+    ay = __fmaf_rn(co.z, dy, __fmul_rn(co.y, dx));
+    const float power = __fmul_rn(-0.5f, __fmaf_rn(dy, ay, __fmul_rn(dx, ax)));
     G = __expf(power);
     alpha = fminf(kAlphaMax, co.w * G);
     return fabsf(dx) <= radius && fabsf(dy) <= radius && power <= 0.f && alpha >= kAlphaMin;

@@ -109,6 +109,15 @@ struct BlendArgs {
     const float4* conic_o;
     const float4* rgb_r;
     float bg[3];
+    // sampled mode (thread-efficient partial rendering, Alg. 3); s_off null
+    // for the full render
+    const long long* s_off;      // [tiles + 1] samples of global tile t: [s_off[t], s_off[t + 1])
+    const uint16_t* s_pix;       // pixel index inside the tile, ly * tw + lx
+    const long long* chunk_off;  // [tiles + 1] first run of order position i; [tiles] = total runs
+    const int* chunk_map;        // [total runs] order position of each run
+    long long chunk_cap;         // entries of chunk_map (runs beyond it are not rendered)
+    // naive partial rendering (Fig. 3b): full strips, pixels with a zero byte idle
+    const uint8_t* pixel_mask;   // [pixels] or null
 };
 // Pixels per lane for a tile size (req > 0: the caller's choice, checked).
 int blend_pixels_per_thread(int tw, int th, int req);
@@ -117,6 +126,20 @@ void launch_blend_forward(const BlendArgs& a, int* counter, float* img, float* f
                           uint2* pixel_stats, cudaStream_t s);
 void launch_blend_backward(const BlendArgs& a, int* counter, const float* dimg, const float* final_T,
                            const uint32_t* n_contrib, float* rec_grad, cudaStream_t s);
+
+// ---- partial.cu ------------------------------------------------------------
+// Pixel selection of the partial render: view v takes pixel (x, y) when the
+// SplitMix64 hash of (seed, x, y) falls in slot v mod `group` of `group`.
+size_t sample_temp_bytes(long long tiles);
+void launch_partial_samples(const DevCam* cams, int V, long long tiles, int tw, int th, int group,
+                            unsigned long long seed, long long* s_off, uint16_t* s_pix, void* tmp, cudaStream_t s);
+// Runs of 32 * ppt samples per tile in the blend's tile order.
+size_t chunk_temp_bytes(long long tiles);
+void launch_sample_chunks(const uint32_t* order, const long long* s_off, long long tiles, int run,
+                          long long* chunk_off, int* chunk_map, long long map_cap, void* tmp, cudaStream_t s);
+// Byte mask [pixels] of the sampled pixels (zeroed first).
+void launch_samples_to_mask(const DevCam* cams, int V, long long tiles, long long pixels, int tw, int th,
+                            const long long* s_off, const uint16_t* s_pix, uint8_t* mask, cudaStream_t s);
 
 // ---- dssim.cu --------------------------------------------------------------
 size_t dssim_temp_bytes(const int* hw, int V);

@@ -437,6 +437,49 @@ __global__ void rect_diff_kernel(const short4* __restrict__ rect, const int* __r
     atomicAdd(d + rc.w * W1 + rc.z, 1);
 }
 
+// The same difference grid accumulated in shared memory: each block adds the
+// corners of a contiguous chunk of records into its own copy of the grid of
+// all views (no contention between blocks), then writes it out as one partial
+// grid; sum_parts_kernel adds the partial grids.  Same-address atomics in L2
+// serialise when many small rectangles share corners; shared-memory atomics
+// spread over 32 banks per SM do not.
+constexpr int RD_PARTS = 304;      // partial grids (2 per SM on 152 SMs)
+constexpr int RD_THREADS = 512;
+constexpr long long RD_MAX_CELLS = 54 * 1024;  // 216 KB of int counters
+
+__global__ void __launch_bounds__(RD_THREADS)
+rect_diff_smem_kernel(const short4* __restrict__ rect, const int* __restrict__ rec_v, uint64_t R,
+                      const DevCam* __restrict__ cams, int cells, int* __restrict__ parts) {
+    extern __shared__ int grid[];
+    for (int c = threadIdx.x; c < cells; c += blockDim.x) grid[c] = 0;
+    __syncthreads();
+    const uint64_t chunk = (R + gridDim.x - 1) / gridDim.x;
+    const uint64_t r0 = (uint64_t)blockIdx.x * chunk;
+    const uint64_t r1 = r0 + chunk < R ? r0 + chunk : R;
+    for (uint64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const short4 rc = rect[r];
+        if (rc.z <= rc.x || rc.w <= rc.y) continue;
+        const DevCam& cam = cams[rec_v[r]];
+        const int W1 = cam.tiles_x + 1;
+        int* d = grid + cam.diff_base;
+        atomicAdd(d + rc.y * W1 + rc.x, 1);
+        atomicAdd(d + rc.y * W1 + rc.z, -1);
+        atomicAdd(d + rc.w * W1 + rc.x, -1);
+        atomicAdd(d + rc.w * W1 + rc.z, 1);
+    }
+    __syncthreads();
+    int* out = parts + (size_t)blockIdx.x * cells;
+    for (int c = threadIdx.x; c < cells; c += blockDim.x) out[c] = grid[c];
+}
+
+__global__ void sum_parts_kernel(const int* __restrict__ parts, int cells, int nparts, int* __restrict__ diff) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cells) return;
+    int acc = 0;
+    for (int p = 0; p < nparts; p++) acc += parts[(size_t)p * cells + c];
+    diff[c] = acc;
+}
+
 // One block per view: prefix sums along rows, then along columns, give the
 // number of records covering each tile.
 __global__ void diff_to_counts_kernel(const DevCam* __restrict__ cams, int* __restrict__ diff,
@@ -614,31 +657,48 @@ void tile_order(const long long* ranges, long long tiles, uint32_t* order, void*
     radix_sort_pairs(ka, ia, kb, ib, order, (uint64_t)tiles, 16, base + 4 * a, s);
 }
 
-size_t tile_count_temp_bytes(const DevCam* host_cams, int V, long long tiles) {
+static long long diff_cells(const DevCam* host_cams, int V) {
     long long cells = 0;
     for (int v = 0; v < V; v++) cells += (long long)(host_cams[v].tiles_x + 1) * (host_cams[v].tiles_y + 1);
+    return cells;
+}
+
+size_t tile_count_temp_bytes(const DevCam* host_cams, int V, long long tiles) {
+    const long long cells = diff_cells(host_cams, V);
     const size_t a = ((size_t)cells * sizeof(int) + 255) / 256 * 256;
     const size_t b = ((size_t)tiles * sizeof(uint32_t) + 255) / 256 * 256;
     const size_t c = ((size_t)(tiles + 1) * sizeof(unsigned long long) + 255) / 256 * 256;
-    return a + b + c + scan_temp_bytes((uint64_t)tiles);
+    const size_t d = cells <= RD_MAX_CELLS ? (size_t)RD_PARTS * a : 0;
+    return a + b + c + d + scan_temp_bytes((uint64_t)tiles);
 }
 
 void tile_ranges_from_rects(const short4* rect, const int* rec_v, uint64_t R, const DevCam* cams,
                             const DevCam* host_cams, int V, long long tiles, long long* ranges, void* tmp,
                             cudaStream_t s) {
-    long long cells = 0;
-    for (int v = 0; v < V; v++) cells += (long long)(host_cams[v].tiles_x + 1) * (host_cams[v].tiles_y + 1);
+    const long long cells = diff_cells(host_cams, V);
+    const size_t a = ((size_t)cells * sizeof(int) + 255) / 256 * 256;
     char* base = static_cast<char*>(tmp);
     int* diff = reinterpret_cast<int*>(base);
-    base += ((size_t)cells * sizeof(int) + 255) / 256 * 256;
+    base += a;
     uint32_t* counts = reinterpret_cast<uint32_t*>(base);
     base += ((size_t)tiles * sizeof(uint32_t) + 255) / 256 * 256;
     unsigned long long* starts = reinterpret_cast<unsigned long long*>(base);
     base += ((size_t)(tiles + 1) * sizeof(unsigned long long) + 255) / 256 * 256;
-    cudaMemsetAsync(diff, 0, (size_t)cells * sizeof(int), s);
-    if (R > 0) {
-        rect_diff_kernel<<<(unsigned)ceil_div_u64(R, 256), 256, 0, s>>>(rect, rec_v, R, cams, diff);
-        note_launches(1);
+    if (cells <= RD_MAX_CELLS) {
+        int* parts = reinterpret_cast<int*>(base);
+        base += (size_t)RD_PARTS * a;
+        const size_t smem = (size_t)cells * sizeof(int);
+        cudaFuncSetAttribute(rect_diff_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        rect_diff_smem_kernel<<<RD_PARTS, RD_THREADS, smem, s>>>(rect, rec_v, R, cams, (int)cells, parts);
+        sum_parts_kernel<<<(unsigned)ceil_div_u64((uint64_t)cells, 256), 256, 0, s>>>(parts, (int)cells, RD_PARTS,
+                                                                                       diff);
+        note_launches(2);
+    } else {
+        cudaMemsetAsync(diff, 0, (size_t)cells * sizeof(int), s);
+        if (R > 0) {
+            rect_diff_kernel<<<(unsigned)ceil_div_u64(R, 256), 256, 0, s>>>(rect, rec_v, R, cams, diff);
+            note_launches(1);
+        }
     }
     diff_to_counts_kernel<<<V, 256, 0, s>>>(cams, diff, counts);
     scan_u32_to_u64(counts, starts, (uint64_t)tiles, base, s);

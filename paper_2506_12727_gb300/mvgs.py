@@ -19,6 +19,14 @@ OK, EINVAL, ENOSPACE, EOVERFLOW, ECUDA, EDEVICE = 0, 1, 2, 3, 4, 5
 GRAD_STRIDE = 12
 
 
+class MemoryBudgetError(RuntimeError):
+    """A batch needs more device memory than the rasterizer may hold."""
+
+    def __init__(self, need_bytes, budget_bytes):
+        super().__init__(f"batch needs {need_bytes} bytes of state + workspace, budget {budget_bytes}")
+        self.need_bytes, self.budget_bytes = need_bytes, budget_bytes
+
+
 class MvgsError(RuntimeError):
     def __init__(self, status, msg, needed=None):
         super().__init__(f"mvgs status {status}: {msg}")
@@ -43,6 +51,13 @@ class Config(ctypes.Structure):
                 ("flags", ctypes.c_uint32), ("pixels_per_thread", ctypes.c_int32)]
 
 
+class Samples(ctypes.Structure):
+    _fields_ = [("offsets", ctypes.c_void_p), ("pixels", ctypes.c_void_p)]
+
+
+FLAG_MASKED_PARTIAL = 1
+
+
 class Capacity(ctypes.Structure):
     _fields_ = [("records", ctypes.c_int64), ("keys", ctypes.c_int64)]
 
@@ -61,7 +76,9 @@ class Layout(ctypes.Structure):
 # every symbol declared in include/mvgs.h
 EXPORTS = ["mvgs_render_layout", "mvgs_render_views", "mvgs_render_views_backward", "mvgs_dssim_workspace_size",
            "mvgs_dssim_loss", "mvgs_adc_accumulate", "mvgs_profile_enable", "mvgs_profile_read", "mvgs_stage_name",
-           "mvgs_launch_count", "mvgs_dssim_loss_noalloc", "mvgs_last_error"]
+           "mvgs_launch_count", "mvgs_dssim_loss_noalloc", "mvgs_last_error",
+           "mvgs_partial_samples_workspace_size", "mvgs_partial_samples", "mvgs_render_views_sampled",
+           "mvgs_render_views_sampled_backward"]
 
 
 def load_library(path: str | None = None):
@@ -74,6 +91,12 @@ def load_library(path: str | None = None):
     lib.mvgs_render_layout.argtypes = [I64, P, I32, P, P, P]
     lib.mvgs_render_views.argtypes = [P, P, I32, P, P, P, P, SZ, P, SZ, P, P]
     lib.mvgs_render_views_backward.argtypes = [P, P, I32, P, P, P, P, SZ, P, SZ, P, P, P, P, P, P, P, P]
+    lib.mvgs_render_views_sampled.argtypes = [P, P, I32, P, P, P, P, P, SZ, P, SZ, P, P]
+    lib.mvgs_render_views_sampled_backward.argtypes = [P, P, I32, P, P, P, P, P, SZ, P, SZ, P, P, P, P, P, P, P,
+                                                       P]
+    lib.mvgs_partial_samples_workspace_size.argtypes = [P, I32, P]
+    lib.mvgs_partial_samples_workspace_size.restype = SZ
+    lib.mvgs_partial_samples.argtypes = [P, I32, P, I32, ctypes.c_uint64, P, P, P, SZ, P]
     lib.mvgs_dssim_workspace_size.argtypes = [P, I32]
     lib.mvgs_dssim_workspace_size.restype = SZ
     lib.mvgs_dssim_loss.argtypes = [P, P, P, I32, ctypes.c_float, P, P, P, SZ, P]
@@ -90,7 +113,8 @@ def load_library(path: str | None = None):
     lib.mvgs_launch_count.argtypes = []
     lib.mvgs_launch_count.restype = I64
     for f in ("mvgs_render_layout", "mvgs_render_views", "mvgs_render_views_backward", "mvgs_dssim_loss",
-              "mvgs_adc_accumulate"):
+              "mvgs_adc_accumulate", "mvgs_render_views_sampled", "mvgs_render_views_sampled_backward",
+              "mvgs_partial_samples"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -185,6 +209,53 @@ def render_views_backward(scene_c, cams_c, cfg, cap, dL_dimages, state, workspac
     _check(st)
 
 
+class SampleSet:
+    """Device arrays of a sample set (mvgs_samples): offsets int64 [tiles + 1]
+    and pixel indices inside the tile (uint16 data held in an int16 tensor)."""
+
+    def __init__(self, offsets: torch.Tensor, pixels: torch.Tensor):
+        self.offsets, self.pixels = offsets, pixels
+        self.c = Samples(_ptr(offsets), _ptr(pixels))
+
+    def pixel_index(self) -> torch.Tensor:
+        """The pixel indices as int64 (0 .. tile_w * tile_h - 1)."""
+        n = int(self.offsets[-1])
+        return self.pixels[:n].to(torch.int64) & 0xFFFF
+
+
+def partial_samples(cams_c, cfg, group: int, seed: int, device="cuda", stream=None) -> SampleSet:
+    """mvgs_partial_samples: view v takes the pixels whose hash slot is v mod group."""
+    L = render_layout(0, cams_c, cfg, Capacity(0, 0))
+    offsets = torch.empty(int(L.tiles) + 1, dtype=torch.int64, device=device)
+    pixels = torch.empty(max(int(L.pixels), 1), dtype=torch.int16, device=device)
+    nbytes = int(_lib.mvgs_partial_samples_workspace_size(cams_c, len(cams_c), ctypes.byref(cfg)))
+    ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device)
+    _check(_lib.mvgs_partial_samples(cams_c, len(cams_c), ctypes.byref(cfg), int(group), ctypes.c_uint64(seed),
+                                     _ptr(offsets), _ptr(pixels), _ptr(ws), ws.numel(), _stream(stream)))
+    return SampleSet(offsets, pixels)
+
+
+def render_views_sampled(scene_c, cams_c, cfg, cap, samples: SampleSet, images, state, workspace, stream=None):
+    needed = Capacity()
+    st = _lib.mvgs_render_views_sampled(ctypes.byref(scene_c), cams_c, len(cams_c), ctypes.byref(cfg),
+                                        ctypes.byref(cap), ctypes.byref(samples.c), _ptr(images), _ptr(state),
+                                        state.numel(), _ptr(workspace), workspace.numel(), ctypes.byref(needed),
+                                        _stream(stream))
+    _check(st, needed)
+    return needed
+
+
+def render_views_sampled_backward(scene_c, cams_c, cfg, cap, samples: SampleSet, dL_dimages, state, workspace,
+                                  grads: dict, g_mean2d=None, e1=None, stream=None):
+    st = _lib.mvgs_render_views_sampled_backward(ctypes.byref(scene_c), cams_c, len(cams_c), ctypes.byref(cfg),
+                                                 ctypes.byref(cap), ctypes.byref(samples.c), _ptr(dL_dimages),
+                                                 _ptr(state), state.numel(), _ptr(workspace), workspace.numel(),
+                                                 _ptr(grads["means"]), _ptr(grads["log_scales"]),
+                                                 _ptr(grads["quats"]), _ptr(grads["opacity_logits"]),
+                                                 _ptr(grads["sh"]), _ptr(g_mean2d), _ptr(e1), _stream(stream))
+    _check(st)
+
+
 def dssim_workspace_size(hw: np.ndarray) -> int:
     hw = np.ascontiguousarray(hw, dtype=np.int32)
     return int(_lib.mvgs_dssim_workspace_size(hw.ctypes.data_as(ctypes.c_void_p), hw.shape[0]))
@@ -236,7 +307,9 @@ class Rasterizer:
     and camera set, growing them (with headroom) when a batch needs more
     records or keys than the current capacity."""
 
-    def __init__(self, cams, tile=(16, 16), bg=(0.0, 0.0, 0.0), device="cuda", headroom=1.15, pixels_per_thread=0):
+    def __init__(self, cams, tile=(16, 16), bg=(0.0, 0.0, 0.0), device="cuda", headroom=1.15, pixels_per_thread=0,
+                 max_bytes=None):
+        self.max_bytes = max_bytes  # cap on state + workspace bytes (None: unlimited)
         self.cams_np = cams
         self.cams_c = make_cameras(cams)
         self.cfg = make_config(tile, bg, pixels_per_thread)
@@ -257,6 +330,12 @@ class Rasterizer:
         cap = Capacity(max(int(records * self.headroom) + 1024, self.cap.records if n == self.n else 0),
                        max(int(keys * self.headroom) + 4096, self.cap.keys if n == self.n else 0))
         L = render_layout(n, self.cams_c, self.cfg, cap)
+        if self.max_bytes is not None and L.state_bytes + L.workspace_bytes > self.max_bytes:
+            # try without headroom before giving up
+            cap = Capacity(max(records, 1), max(keys, 1))
+            L = render_layout(n, self.cams_c, self.cfg, cap)
+            if L.state_bytes + L.workspace_bytes > self.max_bytes:
+                raise MemoryBudgetError(L.state_bytes + L.workspace_bytes, self.max_bytes)
         self.state = None
         self.workspace = None
         self.state = torch.empty(L.state_bytes, dtype=torch.uint8, device=self.device)
@@ -266,15 +345,49 @@ class Rasterizer:
     def reserve(self, n, records, keys):
         self._ensure(n, records, keys)
 
-    def forward(self, scene_c, images=None, stream=None):
+    def held_bytes(self) -> int:
+        return 0 if self.state is None else self.state.numel() + self.workspace.numel()
+
+    def set_cameras(self, cams):
+        """Re-targets the rasterizer to another camera batch, keeping its
+        buffers when they are large enough for the current capacities."""
+        self.cams_np = cams
+        self.cams_c = make_cameras(cams)
+        self.pixels = int(sum(int(w) * int(h) for w, h in zip(cams.width, cams.height)))
+        if self.state is None:
+            return
+        L = render_layout(self.n, self.cams_c, self.cfg, self.cap)
+        if L.state_bytes <= self.state.numel() and L.workspace_bytes <= self.workspace.numel():
+            self.layout = L
+        else:
+            self.state = self.workspace = self.layout = None
+
+    def _cfg(self, masked):
+        if not masked:
+            return self.cfg
+        cfg = Config.from_buffer_copy(self.cfg)
+        cfg.flags = FLAG_MASKED_PARTIAL
+        return cfg
+
+    def sample_set(self, group: int, seed: int, stream=None) -> SampleSet:
+        """Seeded partial-render samples for these cameras and this tile size."""
+        return partial_samples(self.cams_c, self.cfg, group, seed, self.device, stream)
+
+    def forward(self, scene_c, images=None, stream=None, samples: SampleSet | None = None, masked=False):
+        """Full render, or with `samples` only the sampled pixels (Alg. 3; with
+        masked=True through the full strips with idle lanes, Fig. 3b)."""
         n = scene_c.n
         if images is None:
             images = torch.empty(3 * self.pixels, dtype=torch.float32, device=self.device)
         self._ensure(n, max(self.cap.records, 1), max(self.cap.keys, 1))
         for _ in range(4):
             try:
-                self.needed = render_views(scene_c, self.cams_c, self.cfg, self.cap, images, self.state,
-                                           self.workspace, stream)
+                if samples is None:
+                    self.needed = render_views(scene_c, self.cams_c, self.cfg, self.cap, images, self.state,
+                                               self.workspace, stream)
+                else:
+                    self.needed = render_views_sampled(scene_c, self.cams_c, self._cfg(masked), self.cap, samples,
+                                                       images, self.state, self.workspace, stream)
                 return images
             except MvgsError as e:
                 if e.status != ENOSPACE or e.needed is None:
@@ -283,9 +396,14 @@ class Rasterizer:
                              max(e.needed.keys, self.cap.keys))
         raise MvgsError(ENOSPACE, "could not size the buffers")
 
-    def backward(self, scene_c, dL_dimages, grads, g_mean2d=None, e1=None, stream=None):
-        render_views_backward(scene_c, self.cams_c, self.cfg, self.cap, dL_dimages, self.state, self.workspace,
-                              grads, g_mean2d, e1, stream)
+    def backward(self, scene_c, dL_dimages, grads, g_mean2d=None, e1=None, stream=None,
+                 samples: SampleSet | None = None, masked=False):
+        if samples is None:
+            render_views_backward(scene_c, self.cams_c, self.cfg, self.cap, dL_dimages, self.state,
+                                  self.workspace, grads, g_mean2d, e1, stream)
+        else:
+            render_views_sampled_backward(scene_c, self.cams_c, self._cfg(masked), self.cap, samples, dL_dimages,
+                                          self.state, self.workspace, grads, g_mean2d, e1, stream)
 
     # views into the state (intermediate results)
     def _view(self, off, count, dtype, width=1):
