@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-loop", action="store_true", help="skip the per-view launch loop")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrivals per second")
     ap.add_argument("--no-partial", action="store_true",
                     help="skip the partial-rendering comparison (full / masked / thread-efficient)")
     return ap.parse_args()
@@ -264,6 +267,11 @@ def run_ours(args, rank, world):
                        max(1e-9, modes["thread_efficient"]["blend_forward_ms"] +
                            modes["thread_efficient"]["blend_backward_ms"])}
 
+    # ---- serving loop: resident 2M SH-3 scene, Poisson arrivals ----
+    serving = None
+    if not args.no_serve and rank == 0:
+        serving = run_serving(args, torch, mvgs)
+
     # ---- end to end through the C ABI with host buffers ----
     host = {k: v.cpu().pin_memory() for k, v in params.items()}
     host_tgt = tgt.cpu().pin_memory()
@@ -298,6 +306,7 @@ def run_ours(args, rank, world):
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "per_view_loop": loop,
         "partial_rendering": partial,
+        "serving": serving,
         "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in (stages or {}).items() if v[1]},
         "roofline": roof,
         "stage_roofline": per_stage,
@@ -307,6 +316,63 @@ def run_ours(args, rank, world):
         out["cpu_baseline"] = cpu_baseline(args.workload)
     if dist:
         dist.destroy_process_group()
+    return out
+
+
+def run_serving(args, torch, mvgs):
+    """Continuous-batching serving of Poisson requests (1-16 views each, 640x480
+    / 1280x720 / 1920x1080, poses on a radius 3..5 shell) against a resident
+    scene of 2M SH-3 Gaussians; latency from arrival to the completion of the
+    request's batch on the device.
+
+    First the closed-loop capacity (requests/s with the queue always full),
+    then two Poisson traces of about 10 s of work each: at the configured rate
+    (200 req/s, far above one GPU's capacity for this scene: the queue grows
+    and latency measures the backlog) and at 70% of the measured capacity."""
+    from paper_2506_12727_gb300 import serve
+    import time as _time
+    scene = synth.make_scene(2_000_000, 3, seed=synth.SEED_SCENE)
+    params = {k: torch.tensor(getattr(scene, k), device="cuda").contiguous() for k in
+              ("means", "log_scales", "quats", "opacity_logits", "sh")}
+    pool = synth.poisson_requests(400, rate_hz=args.serve_rate)
+    cams = [synth.make_cameras(r["resolutions"], radius=(3.0, 5.0), seed=r["cam_seed"]) for r in pool]
+
+    def server():
+        return serve.Server(params, 3, tile=(16, 64), slots=2, max_views=32, max_pixels=40_000_000,
+                            memory_budget=96 << 30)
+
+    out = {"scene": "2M SH-3 resident", "tile": "16x64", "slots": 2,
+           "latency": "arrival to completion of the request's batch on the device; images stay on the device"}
+    # warm-up and closed-loop capacity
+    srv = server()
+    serve.run_trace(srv, [serve.Request(i, cams[i]) for i in range(6)], [0.0] * 6, realtime=False, timeout_s=120)
+    cap_reqs = [serve.Request(i, cams[i]) for i in range(6, 30)]
+    wall = serve.run_trace(srv, cap_reqs, [0.0] * len(cap_reqs), realtime=False, timeout_s=120)
+    done = [r for r in cap_reqs if r.error is None]
+    cap_rps = len(done) / wall
+    out["capacity"] = {"requests_per_s": cap_rps, "views_per_s": sum(r.views for r in done) / wall,
+                       "requests": len(cap_reqs), "failed": len(cap_reqs) - len(done)}
+    srv.close()
+    traces = {}
+    for name, rate in (("configured_rate", args.serve_rate), ("at_70pct_capacity", 0.7 * cap_rps)):
+        n = int(min(len(pool) - 30, max(8, cap_rps * 10.0)))  # about 10 s of work
+        rng = np.random.default_rng(3)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+        reqs = [serve.Request(30 + i, cams[30 + i]) for i in range(n)]
+        srv = server()
+        t0 = _time.perf_counter()
+        wall = serve.run_trace(srv, reqs, list(arrivals - arrivals[0]), realtime=True, timeout_s=60)
+        srv.close()
+        st = serve.latency_summary(reqs)
+        st.update({"offered_requests_per_s": rate, "wall_s": wall, "views_per_s": st["views"] / wall,
+                   "batches": len(srv.batch_log),
+                   "mean_requests_per_batch": float(np.mean([b[3] for b in srv.batch_log])) if srv.batch_log else 0})
+        traces[name] = st
+    out["traces"] = traces
+    main = traces["configured_rate"]
+    out.update({"p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"], "views_per_s": main["views_per_s"]})
+    del params
+    torch.cuda.empty_cache()
     return out
 
 

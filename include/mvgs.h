@@ -100,7 +100,7 @@ typedef struct mvgs_scene {
 typedef struct mvgs_config {
     int32_t tile_w, tile_h;
     float bg[3];      /* background colour added with the final transmittance */
-    uint32_t flags;   /* 0, or MVGS_FLAG_MASKED_PARTIAL (sampled calls only) */
+    uint32_t flags;   /* MVGS_FLAG_* bits below (0 = none) */
     int32_t pixels_per_thread;  /* blend lanes each own this many pixels of a
                                    tile column, so one warp blends a strip of
                                    tile_w columns by (32 / tile_w) *
@@ -114,6 +114,11 @@ typedef struct mvgs_config {
  * instead of packing the samples into runs (Alg. 3).  Same results; for
  * comparison. */
 #define MVGS_FLAG_MASKED_PARTIAL 1u
+/* cfg->flags bit for the forward calls: also write each rendered pixel's
+ * expected depth sum_i alpha_i T_i z_i (z_i the camera depth of the i-th
+ * blended Gaussian; not divided by the accumulated opacity) into the state
+ * array at layout.off_pixel_depth, for the 3D distance-aware D-SSIM. */
+#define MVGS_FLAG_DEPTH 2u
 
 /* Capacities the caller sized `state` and `workspace` for:
  * records = visible (Gaussian, view) pairs, keys = (record, tile) pairs. */
@@ -146,6 +151,7 @@ typedef struct mvgs_layout {
     size_t off_n_contrib;            /* uint32[pixels]: list position one past the last contributor */
     size_t off_pixel_stats;          /* uint32x2[pixels]: list entries the pixel examined before it
                                         stopped, and the number of Gaussians it blended */
+    size_t off_pixel_depth;          /* float[pixels]: expected depth (with MVGS_FLAG_DEPTH) */
     int64_t tiles;                   /* total tiles over all views                 */
     int64_t pixels;                  /* total pixels over all views                */
 } mvgs_layout;
@@ -237,6 +243,58 @@ mvgs_status mvgs_render_views_sampled_backward(const mvgs_scene* scene, const mv
                                                size_t workspace_bytes, float* g_means, float* g_log_scales,
                                                float* g_quats, float* g_opacity_logits, float* g_sh,
                                                float* g_mean2d, float* e1, mvgs_stream stream);
+
+/* ---- 3D distance-aware D-SSIM (Sec. 5.1.2) on merged images (Fig. 3c) ----
+ * A partially rendered batch puts, at every pixel position, the pixel of one
+ * view of its group into the "merged" image; neighbours there may come from
+ * different viewpoints, so SSIM's window is replaced by a kernel on 3D
+ * distances between the pixels' surface points.  Views are taken in groups
+ * of `group` consecutive views of one resolution (V a multiple of group);
+ * merged image m (packed like the images: [3, H, W] after the previous
+ * merged images) takes pixel (x, y) from view m * group + slot(x, y), the
+ * view that rendered it under mvgs_partial_samples with the same group and
+ * seed. */
+
+/* Scratch bytes of mvgs_merge_views / mvgs_split_merged_grad. */
+size_t mvgs_merge_workspace_size(int32_t V);
+
+/* Builds the merged images.  Inputs (device, packed per view): images and
+ * targets [3 * pixels], and depth_acc and final_T [pixels] from a forward run
+ * with MVGS_FLAG_DEPTH (the state arrays at layout.off_pixel_depth and
+ * off_final_T).  Outputs (device, packed per merged image; any may be NULL
+ * to skip, points and sigma together):
+ *   merged_img, merged_tgt [3, H, W]  the owner view's colour / target;
+ *   points [3, H, W]  surface point X = R^T (z K^-1 (x + 0.5, y + 0.5, 1) - t)
+ *                     of the owner view, z = depth_acc / (1 - final_T);
+ *   sigma  [H, W]     kernel width sigma_px * z / f_x (sigma_px: the 2D
+ *                     window's sigma, 1.5), 0 where 1 - final_T < 1e-3 (no
+ *                     surface point; such a pixel is only its own neighbour). */
+mvgs_status mvgs_merge_views(const mvgs_camera* cams, int32_t V, int32_t group, uint64_t seed, float sigma_px,
+                             const float* images, const float* targets, const float* depth_acc, const float* final_T,
+                             float* merged_img, float* merged_tgt, float* points, float* sigma, void* workspace,
+                             size_t workspace_bytes, mvgs_stream stream);
+
+/* Sends dL/d(merged images) back to the views: each view pixel gets the
+ * merged gradient where it is the owner and 0 elsewhere (dL_dimages is
+ * fully written, packed per view). */
+mvgs_status mvgs_split_merged_grad(const mvgs_camera* cams, int32_t V, int32_t group, uint64_t seed,
+                                   const float* dL_dmerged, float* dL_dimages, void* workspace,
+                                   size_t workspace_bytes, mvgs_stream stream);
+
+/* Scratch bytes of mvgs_dssim3d_loss for M images (hw: host [M, 2]). */
+size_t mvgs_dssim3d_workspace_size(const int32_t* hw, int32_t M);
+
+/* Per-image L_m = (1 - lambda) mean|I - I*| + lambda (1 - mean SSIM*), SSIM*
+ * with K*(p, q) = exp(-|X_q - X_p|^2 / (2 s_p^2)) over the 11x11 pixel
+ * window of p, normalised to sum 1 over the neighbours inside the image with
+ * s > 0 (p itself always counts), C1 = 0.01^2, C2 = 0.03^2; means over the
+ * 3 channels and all pixels.
+ *   img, target, points [3, H, W] and sigma [H, W] per image, packed;
+ *   loss_per_image [M] out; dL_dimg (packed, or NULL) out: d(mean_m L_m)/d img
+ *   with the kernel weights held constant.  Deterministic. */
+mvgs_status mvgs_dssim3d_loss(const float* img, const float* target, const float* points, const float* sigma,
+                              const int32_t* hw, int32_t M, float lambda, float* loss_per_image, float* dL_dimg,
+                              void* workspace, size_t workspace_bytes, mvgs_stream stream);
 
 /* Scratch bytes mvgs_dssim_loss needs for these views (hw: host [V, 2] of
  * (height, width)). */

@@ -159,6 +159,7 @@ def render(cams, P, S, bg=(0.0, 0.0, 0.0), window=None, want_hash=False):
     last = np.zeros(npx, np.int64)
     amb = np.zeros(npx, np.int32)
     chash = np.zeros(npx, np.uint64)
+    depth = np.zeros(npx)
     ca = cams_array(cams)
     bgv = np.asarray(bg, dtype=np.float64)
     ra = _rec_args(P)
@@ -167,9 +168,9 @@ def render(cams, P, S, bg=(0.0, 0.0, 0.0), window=None, want_hash=False):
     win = _window_arg(cams, window)
     lib.orc_render(ctypes.c_int(P["N"]), ctypes.c_int(cams.V), _p(ca), ctypes.c_int(P["tile"][0]),
                    ctypes.c_int(P["tile"][1]), _p(bgv), *[_p(a) for a in ra], _p(ranges), _p(recs), _p(win),
-                   _p(img), _p(T), _p(last), _p(amb), _p(chash))
+                   _p(img), _p(T), _p(last), _p(amb), _p(chash), _p(depth))
     if want_hash:
-        return img, T, last, amb, chash
+        return img, T, last, amb, chash, depth
     return img, T, last, amb
 
 
@@ -246,8 +247,8 @@ def forward(scene, cams, tile=(16, 16), bg=(0.0, 0.0, 0.0), window=None):
     projected records `P`, the sorted lists `S` and the render outputs."""
     P = project(scene, cams, tile)
     S = sort_keys(cams, tile, P["valid"], P["rect"], P["depth"].astype(np.float32), window)
-    img, T, last, amb, chash = render(cams, P, S, bg, window, want_hash=True)
-    return dict(P=P, S=S, img=img, T=T, last=last, amb=amb, chash=chash)
+    img, T, last, amb, chash, depth = render(cams, P, S, bg, window, want_hash=True)
+    return dict(P=P, S=S, img=img, T=T, last=last, amb=amb, chash=chash, depth=depth)
 
 
 def backward(scene, cams, fwd, dimg, tile=(16, 16), bg=(0.0, 0.0, 0.0), window=None):

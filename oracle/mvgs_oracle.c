@@ -484,13 +484,15 @@ typedef struct {
 
 /* Walks one pixel's sorted list.  Fills the contributor list (if given) and
  * returns the number of contributors; writes colour, final T, the list
- * position one past the last contributor, ambiguity bits and (if given) a
- * hash of the contributor ids, so tests can tell when a perturbation changed
- * a discrete decision. */
+ * position one past the last contributor, ambiguity bits, (if given) a hash
+ * of the contributor ids, so tests can tell when a perturbation changed a
+ * discrete decision, and (if given) the expected depth sum alpha T z of the
+ * contributors, the blend of Eq. 1 with each colour replaced by the camera
+ * depth (the predicted depth the 3D D-SSIM of Sec. 5.1.2 lifts pixels with). */
 static int blend_pixel(double px, double py, const int32_t* list, int64_t len, const recs_t* R, const double* bg,
                        double* C, double* Tout, int64_t* last, int* amb, contrib_t* out, int64_t cap,
-                       uint64_t* hash) {
-    double T = 1.0;
+                       uint64_t* hash, double* Dout) {
+    double T = 1.0, D = 0.0;
     uint64_t h = 1469598103934665603ull;
     C[0] = C[1] = C[2] = 0.0;
     *last = 0;
@@ -524,6 +526,7 @@ static int blend_pixel(double px, double py, const int32_t* list, int64_t len, c
         if (fabs(Tn - K_T_MIN) < M_T_REL * K_T_MIN && T * alpha >= M_EFFECT) *amb |= PA_T_MIN;
         if (Tn < K_T_MIN) break;
         for (int ch = 0; ch < 3; ch++) C[ch] += R->rgb[3 * r + ch] * alpha * T;
+        D += R->depth[r] * alpha * T;
         if (out && n < cap) {
             out[n].rec = r;
             out[n].alpha = alpha;
@@ -541,6 +544,7 @@ static int blend_pixel(double px, double py, const int32_t* list, int64_t len, c
     for (int ch = 0; ch < 3; ch++) C[ch] += T * bg[ch];
     *Tout = T;
     if (hash) *hash = h;
+    if (Dout) *Dout = D;
     return n;
 }
 
@@ -583,7 +587,8 @@ static void free_layout(layout_t* L) {
 void orc_render(int N, int V, const double* cams, int tw, int th, const double* bg, const double* xy,
                 const double* conic, const double* opac, const double* rgb, const double* depth,
                 const int32_t* radius, const int32_t* ramb, const int64_t* ranges, const int32_t* recs,
-                const int32_t* window, double* img, double* Tfinal, int64_t* last, int32_t* pamb, uint64_t* chash) {
+                const int32_t* window, double* img, double* Tfinal, int64_t* last, int32_t* pamb, uint64_t* chash,
+                double* depth_out) {
     (void)N;
     layout_t L = make_layout(V, cams, tw, th);
     recs_t R = {xy, conic, opac, rgb, depth, radius, ramb};
@@ -599,8 +604,10 @@ void orc_render(int N, int V, const double* cams, int tw, int th, const double* 
                 int64_t lst;
                 int a;
                 uint64_t h;
-                blend_pixel(x + 0.5, y + 0.5, recs + s, e - s, &R, bg, C, &T, &lst, &a, NULL, 0, &h);
+                double D;
+                blend_pixel(x + 0.5, y + 0.5, recs + s, e - s, &R, bg, C, &T, &lst, &a, NULL, 0, &h, &D);
                 int64_t p = L.pix_base[v] + (int64_t)y * W + x;
+                if (depth_out) depth_out[p] = D;
                 if (chash) chash[p] = h;
                 for (int ch = 0; ch < 3; ch++) img[3 * L.pix_base[v] + (int64_t)ch * W * H + (int64_t)y * W + x] = C[ch];
                 Tfinal[p] = T;
@@ -650,7 +657,7 @@ void orc_render_pixels_bruteforce(int N, int V, const double* cams, const double
         for (int k = 0; k < n; k++) ids[k] = list[k].rec;
         int64_t lst;
         int a;
-        int nc = blend_pixel(x + 0.5, y + 0.5, ids, n, &R, bg, C_out + 3 * i, T_out + i, &lst, &a, NULL, 0, NULL);
+        int nc = blend_pixel(x + 0.5, y + 0.5, ids, n, &R, bg, C_out + 3 * i, T_out + i, &lst, &a, NULL, 0, NULL, NULL);
         ncontrib[i] = nc;
         pamb[i] = a;
     }
@@ -691,7 +698,7 @@ void orc_render_backward(int N, int V, const double* cams, int tw, int th, const
                 double C[3], T;
                 int64_t lst;
                 int a;
-                int n = blend_pixel(x + 0.5, y + 0.5, recs + s, e - s, &R, bg, C, &T, &lst, &a, cl, maxlen, NULL);
+                int n = blend_pixel(x + 0.5, y + 0.5, recs + s, e - s, &R, bg, C, &T, &lst, &a, cl, maxlen, NULL, NULL);
                 double dC[3];
                 for (int ch = 0; ch < 3; ch++)
                     dC[ch] = dimg[3 * L.pix_base[v] + (int64_t)ch * W * H + (int64_t)y * W + x];

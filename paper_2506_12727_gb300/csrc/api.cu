@@ -141,7 +141,8 @@ mvgs_status check_config(const mvgs_config* cfg) {
     const int tw = cfg->tile_w, th = cfg->tile_h;
     const bool side_ok = (tw == 8 || tw == 16 || tw == 32) && (th == 8 || th == 16 || th == 32 || th == 64);
     if (!side_ok) return fail(MVGS_EINVAL, "unsupported tile %dx%d (width 8, 16 or 32; height 8 to 64)", tw, th);
-    if (cfg->flags & ~(uint32_t)MVGS_FLAG_MASKED_PARTIAL) return fail(MVGS_EINVAL, "unknown flags 0x%x", cfg->flags);
+    if (cfg->flags & ~(uint32_t)(MVGS_FLAG_MASKED_PARTIAL | MVGS_FLAG_DEPTH))
+        return fail(MVGS_EINVAL, "unknown flags 0x%x", cfg->flags);
     const int ppt = cfg->pixels_per_thread;
     if (ppt != 0) {
         // a warp covers tile_w columns and (32 / tile_w) * ppt rows of a tile
@@ -215,6 +216,7 @@ mvgs_status make_plan(long long n, const mvgs_camera* cams, int V, const mvgs_co
     L.off_final_T = s.take((size_t)pixels * sizeof(float));
     L.off_n_contrib = s.take((size_t)pixels * sizeof(uint32_t));
     L.off_pixel_stats = s.take((size_t)pixels * 2 * sizeof(uint32_t));
+    L.off_pixel_depth = s.take((size_t)pixels * sizeof(float));
     L.state_bytes = s.off;
     L.tiles = tiles;
     L.pixels = pixels;
@@ -250,7 +252,7 @@ mvgs_status make_plan(long long n, const mvgs_camera* cams, int V, const mvgs_co
     const size_t fwd_bytes = w.off;
     Carver b;
     P.b_cams = b.take((size_t)V * sizeof(DevCam));
-    P.b_grad = b.take(R * kGradStride * sizeof(float));
+    P.b_grad = b.take(R * kGradStride * sizeof(float) + R * 3 * sizeof(double));
     P.b_counter = b.take(sizeof(int));
     P.b_chunk_off = b.take((size_t)(tiles + 1) * sizeof(long long));
     P.b_chunk_map = b.take((size_t)P.chunk_cap * sizeof(int));
@@ -518,6 +520,8 @@ static mvgs_status render_impl(const mvgs_scene* scene, const mvgs_camera* cams,
     ba.conic_o = rec.conic_o;
     ba.rgb_r = rec.rgb_r;
     for (int i = 0; i < 3; i++) ba.bg[i] = cfg->bg[i];
+    ba.rec_depth = rec.depth;
+    ba.depth_out = (cfg->flags & MVGS_FLAG_DEPTH) ? at<float>(state, L.off_pixel_depth) : nullptr;
     {
         StageTimer t(MVGS_STAGE_BLEND_FORWARD, s);
         attach_samples(ba, smp, cfg, P, workspace, P.w_chunk_off, P.w_chunk_map, P.w_chunk_tmp, P.w_mask, s);
@@ -552,9 +556,10 @@ static mvgs_status backward_impl(const mvgs_scene* scene, const mvgs_camera* cam
     void* st_mut = const_cast<void*>(state);  // read only below; RecordArgs carries non-const pointers
     const RecordArgs rec = record_args(st_mut, L);
     float* rec_grad = at<float>(workspace, P.b_grad);
+    double* rec_conic = reinterpret_cast<double*>(rec_grad + (size_t)cap->records * kGradStride);
     {
         StageTimer t(MVGS_STAGE_ZERO_GRADS, s);
-        launch_zero_f32(rec_grad, (size_t)cap->records * kGradStride, s);
+        launch_zero_f32(rec_grad, (size_t)cap->records * (kGradStride + 6), s);  // floats, then the doubles
     }
 
     BlendArgs ba;
@@ -573,15 +578,17 @@ static mvgs_status backward_impl(const mvgs_scene* scene, const mvgs_camera* cam
     ba.conic_o = rec.conic_o;
     ba.rgb_r = rec.rgb_r;
     for (int i = 0; i < 3; i++) ba.bg[i] = cfg->bg[i];
+    ba.rec_depth = rec.depth;
+    ba.depth_out = nullptr;
     {
         StageTimer t(MVGS_STAGE_BLEND_BACKWARD, s);
         attach_samples(ba, smp, cfg, P, workspace, P.b_chunk_off, P.b_chunk_map, P.b_chunk_tmp, P.b_mask, s);
         launch_blend_backward(ba, at<int>(workspace, P.b_counter), dL_dimages, at<float>(state, L.off_final_T),
-                              at<uint32_t>(state, L.off_n_contrib), rec_grad, s);
+                              at<uint32_t>(state, L.off_n_contrib), rec_grad, rec_conic, s);
     }
     {
         StageTimer t(MVGS_STAGE_PREPROCESS_BACKWARD, s);
-        launch_preprocess_backward(scene_args(scene), dcams, V, rec, rec_grad, g_means, g_log_scales, g_quats,
+        launch_preprocess_backward(scene_args(scene), dcams, V, rec, rec_grad, rec_conic, g_means, g_log_scales, g_quats,
                                    g_opacity_logits, g_sh, g_mean2d, e1, s);
     }
     return cuda_check("render backward");
@@ -652,6 +659,104 @@ mvgs_status mvgs_partial_samples(const mvgs_camera* cams, int32_t V, const mvgs_
     launch_partial_samples(dcams, V, P.tiles, cfg->tile_w, cfg->tile_h, group, (unsigned long long)seed,
                            reinterpret_cast<long long*>(offsets), pixels, base + cam_bytes, s);
     return cuda_check("partial samples");
+}
+
+// ---- merged images and the 3D distance-aware D-SSIM -------------------------
+static mvgs_status merge_plan(const mvgs_camera* cams, int32_t V, int32_t group, Plan& P, std::vector<long long>& mb) {
+    if (group < 1 || V < 1 || !cams || V % group) return fail(MVGS_EINVAL, "V must be a positive multiple of group");
+    mvgs_config cfg{};
+    cfg.tile_w = cfg.tile_h = 16;
+    const mvgs_capacity cap{0, 0};
+    mvgs_status st = make_plan(0, cams, V, &cfg, &cap, P);
+    if (st != MVGS_OK) return st;
+    const int M = V / group;
+    mb.assign(M + 1, 0);
+    for (int m = 0; m < M; m++) {
+        for (int k = 1; k < group; k++)
+            if (cams[m * group + k].width != cams[m * group].width || cams[m * group + k].height != cams[m * group].height)
+                return fail(MVGS_EINVAL, "views %d..%d of group %d differ in resolution", m * group, m * group + group - 1, m);
+        mb[m + 1] = mb[m] + (long long)cams[m * group].width * cams[m * group].height;
+    }
+    return MVGS_OK;
+}
+
+size_t mvgs_merge_workspace_size(int32_t V) {
+    if (V < 1) return 0;
+    return 256 + ((size_t)V * sizeof(DevCam) + 255) / 256 * 256 + (size_t)(V + 1) * sizeof(long long);
+}
+
+static mvgs_status merge_upload(const Plan& P, const std::vector<long long>& mb, void* workspace,
+                                size_t workspace_bytes, cudaStream_t s, DevCam** dcams, long long** dmb) {
+    if (!workspace || workspace_bytes < mvgs_merge_workspace_size(P.V))
+        return fail(MVGS_ENOSPACE, "workspace %zu < %zu bytes", workspace_bytes, mvgs_merge_workspace_size(P.V));
+    char* base = reinterpret_cast<char*>(((uintptr_t)workspace + 255) / 256 * 256);
+    *dcams = reinterpret_cast<DevCam*>(base);
+    *dmb = reinterpret_cast<long long*>(base + ((size_t)P.V * sizeof(DevCam) + 255) / 256 * 256);
+    upload_cams(P.cams.data(), P.V, *dcams, s);
+    if (cudaMemcpyAsync(*dmb, mb.data(), mb.size() * sizeof(long long), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return cuda_check("merge upload");
+    return MVGS_OK;
+}
+
+mvgs_status mvgs_merge_views(const mvgs_camera* cams, int32_t V, int32_t group, uint64_t seed, float sigma_px,
+                             const float* images, const float* targets, const float* depth_acc, const float* final_T,
+                             float* merged_img, float* merged_tgt, float* points, float* sigma, void* workspace,
+                             size_t workspace_bytes, mvgs_stream stream) {
+    Plan P;
+    std::vector<long long> mb;
+    mvgs_status st = merge_plan(cams, V, group, P, mb);
+    if (st != MVGS_OK) return st;
+    if ((merged_img && !images) || (merged_tgt && !targets)) return fail(MVGS_EINVAL, "NULL input for a requested output");
+    if ((points != nullptr) != (sigma != nullptr)) return fail(MVGS_EINVAL, "points and sigma go together");
+    if (points && (!depth_acc || !final_T)) return fail(MVGS_EINVAL, "points need depth_acc and final_T");
+    if (points && !(sigma_px > 0.f)) return fail(MVGS_EINVAL, "sigma_px must be > 0");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DevCam* dcams;
+    long long* dmb;
+    if ((st = merge_upload(P, mb, workspace, workspace_bytes, s, &dcams, &dmb)) != MVGS_OK) return st;
+    launch_merge_views(dcams, group, (unsigned long long)seed, sigma_px, mb.back(), dmb, V / group, images, targets,
+                       depth_acc, final_T, merged_img, merged_tgt, points, sigma, s);
+    return cuda_check("merge views");
+}
+
+mvgs_status mvgs_split_merged_grad(const mvgs_camera* cams, int32_t V, int32_t group, uint64_t seed,
+                                   const float* dL_dmerged, float* dL_dimages, void* workspace,
+                                   size_t workspace_bytes, mvgs_stream stream) {
+    Plan P;
+    std::vector<long long> mb;
+    mvgs_status st = merge_plan(cams, V, group, P, mb);
+    if (st != MVGS_OK) return st;
+    if (!dL_dmerged || !dL_dimages) return fail(MVGS_EINVAL, "NULL gradient");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DevCam* dcams;
+    long long* dmb;
+    if ((st = merge_upload(P, mb, workspace, workspace_bytes, s, &dcams, &dmb)) != MVGS_OK) return st;
+    launch_split_merged(dcams, group, (unsigned long long)seed, mb.back(), dmb, V / group, dL_dmerged, dL_dimages, s);
+    return cuda_check("split merged gradient");
+}
+
+size_t mvgs_dssim3d_workspace_size(const int32_t* hw, int32_t M) {
+    if (!hw || M < 1) return 0;
+    return dssim3d_temp_bytes(hw, M);
+}
+
+mvgs_status mvgs_dssim3d_loss(const float* img, const float* target, const float* points, const float* sigma,
+                              const int32_t* hw, int32_t M, float lambda, float* loss_per_image, float* dL_dimg,
+                              void* workspace, size_t workspace_bytes, mvgs_stream stream) {
+    if (!img || !target || !points || !sigma || !hw || !loss_per_image || !workspace)
+        return fail(MVGS_EINVAL, "NULL argument");
+    if (M < 1) return fail(MVGS_EINVAL, "need at least one image");
+    for (int i = 0; i < M; i++)
+        if (hw[2 * i] < 1 || hw[2 * i + 1] < 1) return fail(MVGS_EINVAL, "image %d: empty", i);
+    if (!(lambda >= 0.f && lambda <= 1.f)) return fail(MVGS_EINVAL, "lambda must be in [0, 1]");
+    const size_t need = dssim3d_temp_bytes(hw, M);
+    if (workspace_bytes < need) return fail(MVGS_ENOSPACE, "workspace %zu < %zu bytes", workspace_bytes, need);
+    {
+        StageTimer t(MVGS_STAGE_DSSIM, reinterpret_cast<cudaStream_t>(stream));
+        launch_dssim3d(img, target, points, sigma, hw, M, lambda, loss_per_image, dL_dimg, workspace,
+                       reinterpret_cast<cudaStream_t>(stream));
+    }
+    return cuda_check("dssim3d");
 }
 
 size_t mvgs_dssim_workspace_size(const int32_t* hw, int32_t V) {

@@ -167,25 +167,28 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(Ble
     __shared__ float4 s_co[WARPS_PER_BLOCK][WBATCH];
     __shared__ float4 s_rgb[WARPS_PER_BLOCK][WBATCH];
     __shared__ uint32_t s_pos[WARPS_PER_BLOCK][WBATCH];
+    __shared__ float s_dep[WARPS_PER_BLOCK][WBATCH];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     float2* wxy = s_xy[w];
     float4* wco = s_co[w];
     float4* wrgb = s_rgb[w];
     uint32_t* wpos = s_pos[w];
+    float* wdep = s_dep[w];
+    const bool want_depth = a.depth_out != nullptr;
     constexpr uint32_t ALL = (1u << PPT) - 1u;
     const long long total = SAMPLED ? min(a.chunk_off[a.tiles], a.chunk_cap) : 0;
     Work<PPT> st;
     while (next_work<PPT, SAMPLED>(a, counter, lane, total, st)) {
         const DevCam& cam = *st.cam;
         const long long start = a.ranges[2 * st.gt], end = a.ranges[2 * st.gt + 1];
-        float T[PPT], C0[PPT], C1[PPT], C2[PPT];
+        float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT];
         uint32_t last[PPT], stop[PPT], nblend[PPT];
         uint32_t done = 0;
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
             T[k] = 1.f;
-            C0[k] = C1[k] = C2[k] = 0.f;
+            C0[k] = C1[k] = C2[k] = D[k] = 0.f;
             last[k] = 0;
             stop[k] = (uint32_t)(end - start);  // list position where the pixel stopped
             nblend[k] = 0;
@@ -201,8 +204,9 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(Ble
                 bool hit = false;
                 float2 m;
                 float4 co, cr;
+                uint32_t r = 0;
                 if (idx < end) {
-                    const uint32_t r = a.sorted[idx];
+                    r = a.sorted[idx];
                     m = a.xy[r];
                     co = a.conic_o[r];
                     cr = a.rgb_r[r];
@@ -215,6 +219,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(Ble
                     wco[slot] = co;
                     wrgb[slot] = cr;
                     wpos[slot] = (uint32_t)(idx - start);
+                    if (want_depth) wdep[slot] = a.rec_depth[r];
                 }
                 n += __popc(bal);
             }
@@ -226,6 +231,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(Ble
                 if (!SAMPLED && fabsf(dx0) > cr.w) continue;  // outside the support for the whole column
                 const float4 co = wco[j];
                 const uint32_t pos = wpos[j];
+                const float dep = want_depth ? wdep[j] : 0.f;
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
                     if ((done >> k) & 1u) continue;
@@ -242,6 +248,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(Ble
                     C0[k] = __fmaf_rn(cr.x, wgt, C0[k]);
                     C1[k] = __fmaf_rn(cr.y, wgt, C1[k]);
                     C2[k] = __fmaf_rn(cr.z, wgt, C2[k]);
+                    D[k] = __fmaf_rn(dep, wgt, D[k]);
                     T[k] = Tn;
                     last[k] = pos + 1;
                     nblend[k]++;
@@ -261,6 +268,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(Ble
                 final_T[cam.pix_base + p] = T[k];
                 n_contrib[cam.pix_base + p] = last[k];
                 pixel_stats[cam.pix_base + p] = make_uint2(stop[k], nblend[k]);
+                if (want_depth) a.depth_out[cam.pix_base + p] = D[k];
             }
         }
     }
@@ -288,7 +296,8 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(Bl
                                                                               const float* __restrict__ dimg,
                                                                               const float* __restrict__ final_T,
                                                                               const uint32_t* __restrict__ n_contrib,
-                                                                              float* __restrict__ rec_grad) {
+                                                                              float* __restrict__ rec_grad,
+                                                                              double* __restrict__ rec_conic) {
     __shared__ float2 s_xy[WARPS_PER_BLOCK][WBATCH];
     __shared__ float4 s_co[WARPS_PER_BLOCK][WBATCH];
     __shared__ float4 s_rgb[WARPS_PER_BLOCK][WBATCH];
@@ -407,7 +416,14 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(Bl
                 }
                 if (__ballot_sync(kFull, any) == 0u) continue;
                 const float sum = warp_reduce_scatter16(g, lane);
-                if (adder) atomicAdd(rec_grad + (size_t)kGradStride * wrid[j] + my_val, sum);
+                if (adder) {
+                    // the conic gradients sum terms weighted by dx^2 ~ 1e4 px^2 of both
+                    // signs: they are added across warps in double precision
+                    if (my_val >= 2 && my_val <= 4)
+                        atomicAdd(rec_conic + (size_t)3 * wrid[j] + (my_val - 2), (double)sum);
+                    else
+                        atomicAdd(rec_grad + (size_t)kGradStride * wrid[j] + my_val, sum);
+                }
             }
         }
     }
@@ -469,14 +485,14 @@ void launch_blend_forward(const BlendArgs& a, int* counter, float* img, float* f
 }
 
 void launch_blend_backward(const BlendArgs& a, int* counter, const float* dimg, const float* final_T,
-                           const uint32_t* n_contrib, float* rec_grad, cudaStream_t s) {
+                           const uint32_t* n_contrib, float* rec_grad, double* rec_conic, cudaStream_t s) {
     if (a.tiles == 0) return;
     cudaMemsetAsync(counter, 0, sizeof(int), s);
     const bool sampled = a.s_off != nullptr;
     const long long items = sampled ? (1LL << 40) : a.tiles * a.strips;
 #define MVGS_BB(P, S)                                                                                            \
     blend_backward_kernel<P, S><<<grid_for(blend_backward_kernel<P, S>, items), 32 * WARPS_PER_BLOCK, 0, s>>>(  \
-        a, counter, dimg, final_T, n_contrib, rec_grad)
+        a, counter, dimg, final_T, n_contrib, rec_grad, rec_conic)
 #define MVGS_BB2(P) if (sampled) MVGS_BB(P, true); else MVGS_BB(P, false)
     switch (a.ppt) {
         case 1: MVGS_BB2(1); break;

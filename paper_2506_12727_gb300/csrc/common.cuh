@@ -55,6 +55,22 @@ __device__ __forceinline__ int find_view(const DevCam* cams, int V, long long gt
     return lo;
 }
 
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output number k of the
+// stream seeded with s is mix(s + k * 0x9e3779b97f4a7c15).  The partial-render
+// sample slot of pixel (x, y) in a group of `group` views is
+// floor(group * (h >> 32) / 2^32) with h output number 2^32 y + x + 1.
+__device__ __forceinline__ unsigned long long splitmix64_mix(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ int sample_slot(unsigned long long seed, int x, int y, int group) {
+    const unsigned long long c = ((unsigned long long)y << 32) | (unsigned)x;
+    const unsigned long long h = splitmix64_mix(seed + (c + 1ULL) * 0x9e3779b97f4a7c15ULL);
+    return (int)(((h >> 32) * (unsigned long long)group) >> 32);
+}
+
 // The blend decision and opacity of one (pixel, Gaussian) pair (Eq. 1 with
 // the 3DGS clamp and skip rules and the per-pixel support rule), d = pixel
 // centre minus projected mean, conic (A, B, C) so that the exponent is

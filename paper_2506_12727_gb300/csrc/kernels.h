@@ -51,9 +51,12 @@ void launch_preprocess(const SceneArgs& sc, const DevCam* cams, int V, int tw, i
                        const RecordArgs& rec, uint32_t* depth_keys, uint32_t* rec_ids, uint32_t* tiles_touched,
                        cudaStream_t s);
 void launch_zero_f32(float* p, size_t count, cudaStream_t s);
+// rec_grad: [records, kGradStride] float (mean2d, -, -, -, opacity, rgb, e1 at
+// 0, 1, 5, 6..8, 9); rec_conic: [records, 3] double (conic A, B, C).
 void launch_preprocess_backward(const SceneArgs& sc, const DevCam* cams, int V, const RecordArgs& rec,
-                                const float* rec_grad, float* g_means, float* g_log_scales, float* g_quats,
-                                float* g_logits, float* g_sh, float* out_mean2d, float* out_e1, cudaStream_t s);
+                                const float* rec_grad, const double* rec_conic, float* g_means,
+                                float* g_log_scales, float* g_quats, float* g_logits, float* g_sh,
+                                float* out_mean2d, float* out_e1, cudaStream_t s);
 void launch_adc_accumulate(const long long* rec_off, long long n, const float* g_mean2d, const float* e1,
                            float* accum_e1, float* accum_e2, float* denom, cudaStream_t s);
 
@@ -118,6 +121,9 @@ struct BlendArgs {
     long long chunk_cap;         // entries of chunk_map (runs beyond it are not rendered)
     // naive partial rendering (Fig. 3b): full strips, pixels with a zero byte idle
     const uint8_t* pixel_mask;   // [pixels] or null
+    // optional expected depth sum_i alpha_i T_i z_i per pixel (forward only)
+    const float* rec_depth;      // [records] camera depth
+    float* depth_out;            // [pixels] or null
 };
 // Pixels per lane for a tile size (req > 0: the caller's choice, checked).
 int blend_pixels_per_thread(int tw, int th, int req);
@@ -125,7 +131,7 @@ int blend_pixels_per_thread(int tw, int th, int req);
 void launch_blend_forward(const BlendArgs& a, int* counter, float* img, float* final_T, uint32_t* n_contrib,
                           uint2* pixel_stats, cudaStream_t s);
 void launch_blend_backward(const BlendArgs& a, int* counter, const float* dimg, const float* final_T,
-                           const uint32_t* n_contrib, float* rec_grad, cudaStream_t s);
+                           const uint32_t* n_contrib, float* rec_grad, double* rec_conic, cudaStream_t s);
 
 // ---- partial.cu ------------------------------------------------------------
 // Pixel selection of the partial render: view v takes pixel (x, y) when the
@@ -140,6 +146,18 @@ void launch_sample_chunks(const uint32_t* order, const long long* s_off, long lo
 // Byte mask [pixels] of the sampled pixels (zeroed first).
 void launch_samples_to_mask(const DevCam* cams, int V, long long tiles, long long pixels, int tw, int th,
                             const long long* s_off, const uint16_t* s_pix, uint8_t* mask, cudaStream_t s);
+
+// ---- dssim3d.cu -------------------------------------------------------------
+size_t dssim3d_temp_bytes(const int* hw, int M);
+void launch_dssim3d(const float* img, const float* target, const float* points, const float* sigma, const int* hw,
+                    int M, float lambda, float* loss, float* dimg, void* tmp, cudaStream_t s);
+// mbase: device [M + 1] first pixel of each merged image; cams: device, all V views
+void launch_merge_views(const DevCam* cams, int group, unsigned long long seed, float sigma_px, long long merged_pix,
+                        const long long* mbase, int M, const float* images, const float* targets,
+                        const float* depth_acc, const float* final_T, float* out_img, float* out_tgt, float* out_pts,
+                        float* out_sig, cudaStream_t s);
+void launch_split_merged(const DevCam* cams, int group, unsigned long long seed, long long merged_pix,
+                         const long long* mbase, int M, const float* dmerged, float* dimg, cudaStream_t s);
 
 // ---- dssim.cu --------------------------------------------------------------
 size_t dssim_temp_bytes(const int* hw, int V);

@@ -16,19 +16,8 @@
 namespace mvgs {
 namespace {
 
-constexpr unsigned long long kGolden = 0x9e3779b97f4a7c15ULL;
-
-__device__ __forceinline__ unsigned long long splitmix64_mix(unsigned long long z) {
-    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
-    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
-    return z ^ (z >> 31);
-}
-
 __device__ __forceinline__ bool sampled(unsigned long long seed, int x, int y, int group, int v) {
-    const unsigned long long c = ((unsigned long long)y << 32) | (unsigned)x;
-    const unsigned long long h = splitmix64_mix(seed + (c + 1ULL) * kGolden);
-    const unsigned slot = (unsigned)(((h >> 32) * (unsigned long long)group) >> 32);
-    return slot == (unsigned)(v % group);
+    return sample_slot(seed, x, y, group) == v % group;
 }
 
 struct TileGeom {

@@ -320,6 +320,7 @@ __global__ void zero_kernel(float4* __restrict__ p, size_t n4) {
 template <int DEG>
 __global__ void __launch_bounds__(128) preprocess_backward_kernel(SceneArgs sc, const DevCam* __restrict__ cams,
                                                                   RecordArgs rec, const float* __restrict__ rg,
+                                                                  const double* __restrict__ rc,
                                                                   float* __restrict__ g_means,
                                                                   float* __restrict__ g_log_scales,
                                                                   float* __restrict__ g_quats,
@@ -347,19 +348,24 @@ __global__ void __launch_bounds__(128) preprocess_backward_kernel(SceneArgs sc, 
         const float4 q0 = *reinterpret_cast<const float4*>(rg + kGradStride * r);
         const float4 q1 = *reinterpret_cast<const float4*>(rg + kGradStride * r + 4);
         const float4 q2 = *reinterpret_cast<const float4*>(rg + kGradStride * r + 8);
-        const float gx = q0.x, gy = q0.y, gA = q0.z, gB = q0.w, gC = q1.x, gop = q1.y;
+        const float gx = q0.x, gy = q0.y, gop = q1.y;
+        const float gA = (float)rc[3 * r], gB = (float)rc[3 * r + 1], gC = (float)rc[3 * r + 2];
         const float grgb_raw[3] = {q1.z, q1.w, q2.x};
         if (out_mean2d) {
             out_mean2d[2 * r] = gx;
             out_mean2d[2 * r + 1] = gy;
         }
         if (out_e1) out_e1[r] = q2.y;
-        // conic (A, B, C) = (c, -b, a) / det  ->  (a, b, c)
-        const float a = P.a, b = P.b, c = P.c;
-        const float id = 1.f / P.det, id2 = id * id;
-        const float ga = gA * (-c * c * id2) + gB * (b * c * id2) + gC * (id - a * c * id2);
-        const float gb = gA * (2.f * b * c * id2) + gB * (-id - 2.f * b * b * id2) + gC * (2.f * a * b * id2);
-        const float gc = gA * (id - a * c * id2) + gB * (a * b * id2) + gC * (-a * a * id2);
+        // conic Q = Sigma'^-1 = [[A, B], [B, C]] = [[c, -b], [-b, a]] / det; with
+        // dQ = -Q dSigma' Q, dL/dSigma' = -Q G Q for G = [[gA, gB/2], [gB/2, gC]]
+        // (gB is the derivative w.r.t. B filling both off-diagonal entries, and
+        // gb likewise w.r.t. b).  Written in Q, no term cancels as the
+        // expansion in (a, b, c) / det does when b is small.
+        const float id = 1.f / P.det;
+        const float QA = P.c * id, QB = -P.b * id, QC = P.a * id;
+        const float ga = -(QA * QA * gA + QA * QB * gB + QB * QB * gC);
+        const float gb = -(2.f * QA * QB * gA + (QA * QC + QB * QB) * gB + 2.f * QB * QC * gC);
+        const float gc = -(QB * QB * gA + QB * QC * gB + QC * QC * gC);
         // Sigma' = T Sigma T^T: dL/dSigma += T^T G2 T with G2 = [[ga, gb/2], [gb/2, gc]]
         const float h = 0.5f * gb;
         float GT[6];  // G2 T (2x3)
@@ -540,14 +546,15 @@ void launch_zero_f32(float* p, size_t count, cudaStream_t s) {
 }
 
 void launch_preprocess_backward(const SceneArgs& sc, const DevCam* cams, int V, const RecordArgs& rec,
-                                const float* rec_grad, float* g_means, float* g_log_scales, float* g_quats,
-                                float* g_logits, float* g_sh, float* out_mean2d, float* out_e1, cudaStream_t s) {
+                                const float* rec_grad, const double* rec_conic, float* g_means,
+                                float* g_log_scales, float* g_quats, float* g_logits, float* g_sh, float* out_mean2d,
+                                float* out_e1, cudaStream_t s) {
     (void)V;
     if (sc.n == 0) return;
     const unsigned nb = blocks_for(sc.n, 128);
 #define MVGS_PB(D)                                                                                                 \
-    preprocess_backward_kernel<D><<<nb, 128, 0, s>>>(sc, cams, rec, rec_grad, g_means, g_log_scales, g_quats,     \
-                                                     g_logits, g_sh, out_mean2d, out_e1)
+    preprocess_backward_kernel<D><<<nb, 128, 0, s>>>(sc, cams, rec, rec_grad, rec_conic, g_means, g_log_scales,    \
+                                                     g_quats, g_logits, g_sh, out_mean2d, out_e1)
     switch (sc.sh_degree) {
         case 0: MVGS_PB(0); break;
         case 1: MVGS_PB(1); break;

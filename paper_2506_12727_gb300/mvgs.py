@@ -56,6 +56,7 @@ class Samples(ctypes.Structure):
 
 
 FLAG_MASKED_PARTIAL = 1
+FLAG_DEPTH = 2
 
 
 class Capacity(ctypes.Structure):
@@ -65,7 +66,7 @@ class Capacity(ctypes.Structure):
 _LAYOUT_FIELDS = ["state_bytes", "workspace_bytes", "off_counts", "off_rec_offsets", "off_rec_gauss", "off_rec_view",
                   "off_rec_xy", "off_rec_conic_opacity", "off_rec_rgb", "off_rec_clamp", "off_rec_depth",
                   "off_rec_rect", "off_sorted_records", "off_tile_ranges", "off_tile_order", "off_final_T",
-                  "off_n_contrib", "off_pixel_stats"]
+                  "off_n_contrib", "off_pixel_stats", "off_pixel_depth"]
 
 
 class Layout(ctypes.Structure):
@@ -78,7 +79,8 @@ EXPORTS = ["mvgs_render_layout", "mvgs_render_views", "mvgs_render_views_backwar
            "mvgs_dssim_loss", "mvgs_adc_accumulate", "mvgs_profile_enable", "mvgs_profile_read", "mvgs_stage_name",
            "mvgs_launch_count", "mvgs_dssim_loss_noalloc", "mvgs_last_error",
            "mvgs_partial_samples_workspace_size", "mvgs_partial_samples", "mvgs_render_views_sampled",
-           "mvgs_render_views_sampled_backward"]
+           "mvgs_render_views_sampled_backward", "mvgs_merge_workspace_size", "mvgs_merge_views",
+           "mvgs_split_merged_grad", "mvgs_dssim3d_workspace_size", "mvgs_dssim3d_loss"]
 
 
 def load_library(path: str | None = None):
@@ -97,6 +99,13 @@ def load_library(path: str | None = None):
     lib.mvgs_partial_samples_workspace_size.argtypes = [P, I32, P]
     lib.mvgs_partial_samples_workspace_size.restype = SZ
     lib.mvgs_partial_samples.argtypes = [P, I32, P, I32, ctypes.c_uint64, P, P, P, SZ, P]
+    lib.mvgs_merge_workspace_size.argtypes = [I32]
+    lib.mvgs_merge_workspace_size.restype = SZ
+    lib.mvgs_merge_views.argtypes = [P, I32, I32, ctypes.c_uint64, ctypes.c_float, P, P, P, P, P, P, P, P, P, SZ, P]
+    lib.mvgs_split_merged_grad.argtypes = [P, I32, I32, ctypes.c_uint64, P, P, P, SZ, P]
+    lib.mvgs_dssim3d_workspace_size.argtypes = [P, I32]
+    lib.mvgs_dssim3d_workspace_size.restype = SZ
+    lib.mvgs_dssim3d_loss.argtypes = [P, P, P, P, P, I32, ctypes.c_float, P, P, P, SZ, P]
     lib.mvgs_dssim_workspace_size.argtypes = [P, I32]
     lib.mvgs_dssim_workspace_size.restype = SZ
     lib.mvgs_dssim_loss.argtypes = [P, P, P, I32, ctypes.c_float, P, P, P, SZ, P]
@@ -114,7 +123,7 @@ def load_library(path: str | None = None):
     lib.mvgs_launch_count.restype = I64
     for f in ("mvgs_render_layout", "mvgs_render_views", "mvgs_render_views_backward", "mvgs_dssim_loss",
               "mvgs_adc_accumulate", "mvgs_render_views_sampled", "mvgs_render_views_sampled_backward",
-              "mvgs_partial_samples"):
+              "mvgs_partial_samples", "mvgs_merge_views", "mvgs_split_merged_grad", "mvgs_dssim3d_loss"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -256,6 +265,34 @@ def render_views_sampled_backward(scene_c, cams_c, cfg, cap, samples: SampleSet,
     _check(st)
 
 
+def merge_views(cams_c, group, seed, images=None, targets=None, depth_acc=None, final_T=None, merged_img=None,
+                merged_tgt=None, points=None, sigma=None, sigma_px=1.5, stream=None):
+    """mvgs_merge_views (outputs are caller tensors; None skips)."""
+    ws = torch.empty(int(_lib.mvgs_merge_workspace_size(len(cams_c))), dtype=torch.uint8, device="cuda")
+    _check(_lib.mvgs_merge_views(cams_c, len(cams_c), int(group), ctypes.c_uint64(seed), ctypes.c_float(sigma_px),
+                                 _ptr(images), _ptr(targets), _ptr(depth_acc), _ptr(final_T), _ptr(merged_img),
+                                 _ptr(merged_tgt), _ptr(points), _ptr(sigma), _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def split_merged_grad(cams_c, group, seed, dL_dmerged, dL_dimages, stream=None):
+    ws = torch.empty(int(_lib.mvgs_merge_workspace_size(len(cams_c))), dtype=torch.uint8, device="cuda")
+    _check(_lib.mvgs_split_merged_grad(cams_c, len(cams_c), int(group), ctypes.c_uint64(seed), _ptr(dL_dmerged),
+                                       _ptr(dL_dimages), _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def dssim3d_workspace_size(hw: np.ndarray) -> int:
+    hw = np.ascontiguousarray(hw, dtype=np.int32)
+    return int(_lib.mvgs_dssim3d_workspace_size(hw.ctypes.data_as(ctypes.c_void_p), hw.shape[0]))
+
+
+def dssim3d_loss(img, target, points, sigma, hw, lam, loss_per_image, dL_dimg, workspace, stream=None):
+    hw = np.ascontiguousarray(hw, dtype=np.int32)
+    _check(_lib.mvgs_dssim3d_loss(_ptr(img), _ptr(target), _ptr(points), _ptr(sigma),
+                                  hw.ctypes.data_as(ctypes.c_void_p), hw.shape[0], ctypes.c_float(lam),
+                                  _ptr(loss_per_image), _ptr(dL_dimg), _ptr(workspace), workspace.numel(),
+                                  _stream(stream)))
+
+
 def dssim_workspace_size(hw: np.ndarray) -> int:
     hw = np.ascontiguousarray(hw, dtype=np.int32)
     return int(_lib.mvgs_dssim_workspace_size(hw.ctypes.data_as(ctypes.c_void_p), hw.shape[0]))
@@ -362,20 +399,23 @@ class Rasterizer:
         else:
             self.state = self.workspace = self.layout = None
 
-    def _cfg(self, masked):
-        if not masked:
+    def _cfg(self, masked=False, depth=False):
+        if not masked and not depth:
             return self.cfg
         cfg = Config.from_buffer_copy(self.cfg)
-        cfg.flags = FLAG_MASKED_PARTIAL
+        cfg.flags = (FLAG_MASKED_PARTIAL if masked else 0) | (FLAG_DEPTH if depth else 0)
         return cfg
 
     def sample_set(self, group: int, seed: int, stream=None) -> SampleSet:
         """Seeded partial-render samples for these cameras and this tile size."""
         return partial_samples(self.cams_c, self.cfg, group, seed, self.device, stream)
 
-    def forward(self, scene_c, images=None, stream=None, samples: SampleSet | None = None, masked=False):
+    def forward(self, scene_c, images=None, stream=None, samples: SampleSet | None = None, masked=False,
+                depth=False):
         """Full render, or with `samples` only the sampled pixels (Alg. 3; with
-        masked=True through the full strips with idle lanes, Fig. 3b)."""
+        masked=True through the full strips with idle lanes, Fig. 3b).  With
+        depth=True the expected depth of each rendered pixel is written too
+        (records()["depth_acc"])."""
         n = scene_c.n
         if images is None:
             images = torch.empty(3 * self.pixels, dtype=torch.float32, device=self.device)
@@ -383,11 +423,11 @@ class Rasterizer:
         for _ in range(4):
             try:
                 if samples is None:
-                    self.needed = render_views(scene_c, self.cams_c, self.cfg, self.cap, images, self.state,
-                                               self.workspace, stream)
+                    self.needed = render_views(scene_c, self.cams_c, self._cfg(False, depth), self.cap, images,
+                                               self.state, self.workspace, stream)
                 else:
-                    self.needed = render_views_sampled(scene_c, self.cams_c, self._cfg(masked), self.cap, samples,
-                                                       images, self.state, self.workspace, stream)
+                    self.needed = render_views_sampled(scene_c, self.cams_c, self._cfg(masked, depth), self.cap,
+                                                       samples, images, self.state, self.workspace, stream)
                 return images
             except MvgsError as e:
                 if e.status != ENOSPACE or e.needed is None:
@@ -429,4 +469,5 @@ class Rasterizer:
             final_T=self._view(L.off_final_T, int(L.pixels), torch.float32),
             n_contrib=self._view(L.off_n_contrib, int(L.pixels), torch.int32),
             pixel_stats=self._view(L.off_pixel_stats, int(L.pixels), torch.int32, 2),
+            depth_acc=self._view(L.off_pixel_depth, int(L.pixels), torch.float32),
             counts=self._view(L.off_counts, 4, torch.int64))

@@ -15,8 +15,12 @@ state/workspace buffers:
   - admission by memory: every worker may hold at most `memory_budget /
     slots` bytes of state and workspace.  A batch whose record and key counts
     (the library's cheap count passes report them before anything is
-    allocated) need more is split in two, the second half going back to the
-    front of the queue; a single request that does not fit alone is failed.
+    allocated) need more -- or more keys than one call can index (2^32) -- is
+    split in two, the second half going back to the front of the queue; a
+    single request that does not fit is rendered a part of its views at a
+    time, and fails only if one of its views does not fit alone;
+  - a failure inside a batch fails that batch's requests (with the message)
+    and the worker carries on.
 
 Each view is rendered with exactly the arithmetic it would get alone (the
 batch only adds other views' keys to the sort), so a request's images do not
@@ -109,6 +113,18 @@ class Server:
         for w in self.workers:
             w.join()
 
+    def cancel_pending(self, reason="cancelled"):
+        """Fails every request still waiting in the queue."""
+        with self.cv:
+            pending = list(self.queue)
+            self.queue.clear()
+        t = time.perf_counter()
+        for r in pending:
+            r.error = reason
+            r.t_done = t
+            r.done.set()
+        return len(pending)
+
     # ---- workers ----
     def _take_batch(self):
         """Oldest requests first, up to the view and pixel limits (at least one)."""
@@ -135,32 +151,74 @@ class Server:
                 batch = self._take_batch()
                 bid = self.batches
                 self.batches += 1
-            rz = self._render(batch, bid, stream, rz)
+            try:
+                rz = self._render(batch, bid, stream, rz)
+            except Exception as e:  # a failed batch fails its requests, not the server
+                rz = None
+                torch.cuda.empty_cache()
+                t = time.perf_counter()
+                for r in batch:
+                    if not r.done.is_set():
+                        r.error = f"{type(e).__name__}: {e}"
+                        r.t_done = t
+                        r.done.set()
 
-    def _render(self, batch, bid, stream, rz):
-        cams = CameraBatch([r.cams for r in batch])
+    @staticmethod
+    def _too_big(e):
+        return isinstance(e, mvgs.MemoryBudgetError) or (isinstance(e, mvgs.MvgsError) and
+                                                          e.status == mvgs.EOVERFLOW)
+
+    def _forward(self, cams, stream, rz):
+        """One library call for a camera batch; returns (images, ms, rz)."""
         with torch.cuda.stream(stream):
             if rz is None:
                 rz = mvgs.Rasterizer(cams, tile=self.tile, bg=self.bg, device=self.device,
                                      pixels_per_thread=self.ppt, max_bytes=self.slot_bytes)
             else:
                 rz.set_cameras(cams)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
             try:
-                ev0 = torch.cuda.Event(enable_timing=True)
-                ev1 = torch.cuda.Event(enable_timing=True)
-                ev0.record(stream)
                 img = rz.forward(self.scene_c, stream=stream)
-                ev1.record(stream)
-                stream.synchronize()
-            except mvgs.MemoryBudgetError as e:
+            except Exception:
                 rz.state = rz.workspace = rz.layout = None
                 torch.cuda.empty_cache()
-                if len(batch) == 1:
-                    r = batch[0]
-                    r.error = str(e)
-                    r.t_done = time.perf_counter()
-                    r.done.set()
-                    return rz
+                raise
+            ev1.record(stream)
+            stream.synchronize()
+        return img, ev0.elapsed_time(ev1), rz
+
+    def _render_request_in_parts(self, r, stream, rz):
+        """A request too large for one call: its views a part at a time."""
+        parts, ms = [], 0.0
+        todo = [list(range(r.views))]
+        while todo:
+            idx = todo.pop(0)
+            sub = CameraBatch([_subset(r.cams, idx)])
+            try:
+                img, t, rz = self._forward(sub, stream, rz)
+            except Exception as e:
+                if not self._too_big(e) or len(idx) == 1:
+                    raise
+                half = len(idx) // 2
+                todo[:0] = [idx[:half], idx[half:]]
+                continue
+            parts.append(img.clone())
+            ms += t
+        return torch.cat(parts), ms, rz
+
+    def _render(self, batch, bid, stream, rz):
+        cams = CameraBatch([r.cams for r in batch])
+        try:
+            img, ms, rz = self._forward(cams, stream, rz)
+        except Exception as e:
+            if not self._too_big(e):
+                raise
+            rz = None
+            if len(batch) == 1:
+                img, ms, rz = self._render_request_in_parts(batch[0], stream, rz)
+            else:
                 # split: render the first half now, requeue the rest at the front
                 half = len(batch) // 2
                 with self.cv:
@@ -179,13 +237,23 @@ class Server:
             r.done.set()
         with self.cv:
             self.batch_log.append((bid, cams.V, int(np.sum(cams.width.astype(np.int64) * cams.height)), len(batch),
-                                   ev0.elapsed_time(ev1)))
+                                   ms))
         return rz
 
 
-def run_trace(server: Server, requests, arrivals_s, realtime=True):
+def _subset(cams, idx):
+    """The views `idx` of a camera set (same fields)."""
+    out = CameraBatch([cams])
+    for f in _CAM_FIELDS:
+        setattr(out, f, getattr(out, f)[idx])
+    return out
+
+
+def run_trace(server: Server, requests, arrivals_s, realtime=True, timeout_s=None):
     """Submits requests at their arrival times (seconds from now) and waits for
-    all of them; returns the wall time of the whole trace in seconds."""
+    all of them, or until `timeout_s` after the start, when requests still
+    queued are failed ("timeout") and those on the GPU are waited for; returns
+    the wall time of the whole trace in seconds."""
     t0 = time.perf_counter()
     for r, ta in zip(requests, arrivals_s):
         if realtime:
@@ -194,13 +262,21 @@ def run_trace(server: Server, requests, arrivals_s, realtime=True):
                 time.sleep(dt)
         server.submit(r)
     for r in requests:
-        r.done.wait()
+        left = None if timeout_s is None else t0 + timeout_s - time.perf_counter()
+        if left is not None and left <= 0:
+            server.cancel_pending("timeout")
+            left = None
+        if not r.done.wait(left):
+            server.cancel_pending("timeout")
+            r.done.wait()
     return time.perf_counter() - t0
 
 
 def latency_summary(requests) -> dict:
-    lat = np.array([r.latency for r in requests if r.error is None]) * 1e3
-    views = sum(r.views for r in requests if r.error is None)
-    return {"requests": len(requests), "failed": sum(r.error is not None for r in requests),
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "views": int(views)}
+    ok = [r for r in requests if r.error is None]
+    lat = np.array([r.latency for r in ok]) * 1e3
+    views = sum(r.views for r in ok)
+    return {"requests": len(requests), "completed": len(ok), "failed": len(requests) - len(ok),
+            "p50_ms": float(np.percentile(lat, 50)) if len(ok) else None,
+            "p99_ms": float(np.percentile(lat, 99)) if len(ok) else None,
+            "mean_ms": float(lat.mean()) if len(ok) else None, "views": int(views)}

@@ -56,3 +56,22 @@ def assert_close_frac(got, ref, rtol, atol, what, max_bad=0):
         i = np.unravel_index(np.argmax(err - (atol + rtol * np.abs(ref))), err.shape)
         raise AssertionError(f"{what}: {nb} of {err.size} entries outside tolerance (rtol={rtol}, atol={atol}); "
                              f"worst at {i}: got {got[i]!r} ref {ref[i]!r}")
+
+
+def assert_close_rows(got, ref, rtol, atol, what, max_bad=0):
+    """Like assert_close_frac, with the relative part taken against the norm of
+    each Gaussian's gradient vector for the tensor (the row), not the single
+    component: a component much smaller than its row's norm comes out of
+    cancelling float32 terms of the row's size and is only that accurate."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    g2 = got.reshape(got.shape[0], -1)
+    r2 = ref.reshape(ref.shape[0], -1)
+    err = np.abs(g2 - r2)
+    lim = atol + rtol * np.linalg.norm(r2, axis=1, keepdims=True)
+    bad = err > lim
+    nb = int(bad.sum())
+    if nb > max_bad:
+        i = np.unravel_index(np.argmax(err - lim), err.shape)
+        raise AssertionError(f"{what}: {nb} of {err.size} entries outside tolerance (rtol={rtol} of the row norm, "
+                             f"atol={atol}); worst at {i}: got {g2[i]!r} ref {r2[i]!r}")

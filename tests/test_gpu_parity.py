@@ -27,9 +27,20 @@ AMB_FWD = oracle.PA_FORWARD
 AMB_ALL = 0xFF
 
 
+def _large_gaussians():
+    # few Gaussians of about 0.2 units (radii of 40-150 px): gradients that
+    # sum many pixels at large offsets from the mean
+    rng = np.random.default_rng(3)
+    sc = synth.make_scene(40, 3, seed=11)
+    sc.log_scales[:] = rng.normal(-1.5, 0.3, size=sc.log_scales.shape)
+    sc.opacity_logits[:] = rng.normal(0.5, 0.5, size=sc.opacity_logits.shape)
+    return sc, synth.make_cameras([(196, 160), (160, 196)], radius=4.0, seed=5)
+
+
 def _small_cases():
     # several tiles in each direction and ragged image edges
     return {
+        "large_gaussians_sh3": _large_gaussians(),
         "single_view_10k_sh0": (synth.make_scene(10_000, 0), synth.make_cameras([(128, 128)], radius=3.0)),
         "multiview_sh3_ragged": (synth.make_scene(6_000, 3, seed=5),
                                  synth.make_cameras([(150, 97), (64, 130), (201, 45)], radius=4.0, seed=6)),
