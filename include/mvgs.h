@@ -296,6 +296,53 @@ mvgs_status mvgs_dssim3d_loss(const float* img, const float* target, const float
                               const int32_t* hw, int32_t M, float lambda, float* loss_per_image, float* dL_dimg,
                               void* workspace, size_t workspace_bytes, mvgs_stream stream);
 
+/* ---- training-loop pieces: multi-view densification (Sec. 5.2.2) and Adam ----
+ * Thresholds in the parameters' own spaces; decisions per Gaussian, taken in
+ * double precision from the float32 inputs:
+ *   mean E_k = accum_E_k / denom (0 where denom = 0);
+ *   large    = max_i log_scale_i > log_dense_extent;
+ *   pruned   = opacity_logit < prune_logit (the supplement multiplies the
+ *              opacity threshold by the views per iteration);
+ *   split    = !pruned && large && mean E_1 >= split_threshold;
+ *   cloned   = !pruned && !large && mean E_2 >= clone_threshold
+ *   (E_1 is good at splitting and E_2 at cloning, Sec. 5.2.2). */
+typedef struct mvgs_densify_params {
+    double split_threshold;
+    double clone_threshold;
+    double prune_logit;
+    double log_dense_extent;
+} mvgs_densify_params;
+
+size_t mvgs_densify_workspace_size(int64_t n);
+
+/* One densification step.  Outputs, ordered by source Gaussian: none for a
+ * pruned Gaussian; for a split one two children with mean mu + R(q)(s * z_k)
+ * (z = normals [n, 2, 3], the caller's standard normal samples), log-scale
+ * reduced by ln 1.6 and the rest copied; for a cloned one the Gaussian and a
+ * copy; else the Gaussian.  out_* are device arrays of `capacity` Gaussians
+ * (same layouts as the scene); out_src [capacity] int64 source index and
+ * out_kind [capacity] int32 (0 the Gaussian itself, 1 a clone's copy, 2 a
+ * split child) may be NULL.  Synchronises the stream once to read the output
+ * count into *n_out; if it exceeds `capacity`, returns MVGS_ENOSPACE (with
+ * *n_out set) and writes nothing. */
+mvgs_status mvgs_densify(const mvgs_scene* scene, const float* accum_e1, const float* accum_e2, const float* denom,
+                         const float* normals, const mvgs_densify_params* params, int64_t capacity,
+                         float* out_means, float* out_log_scales, float* out_quats, float* out_opacity_logits,
+                         float* out_sh, int64_t* out_src, int32_t* out_kind, int64_t* n_out, void* workspace,
+                         size_t workspace_bytes, mvgs_stream stream);
+
+/* Carries a per-Gaussian array (`width` floats each, e.g. optimiser moments)
+ * through a densification step: out[d] = in[src[d]] where kind[d] == 0, else
+ * zeros. */
+mvgs_status mvgs_densify_carry(int64_t n_out, const int64_t* src, const int32_t* kind, int32_t width,
+                               const float* in, float* out, mvgs_stream stream);
+
+/* Adam (Kingma & Ba 2015) with bias correction on `count` floats in place:
+ * m = b1 m + (1 - b1) g; v = b2 v + (1 - b2) g^2;
+ * p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).  step >= 1. */
+mvgs_status mvgs_adam_step(int64_t count, float* param, const float* grad, float* m, float* v, float lr, float beta1,
+                           float beta2, float eps, int32_t step, mvgs_stream stream);
+
 /* Scratch bytes mvgs_dssim_loss needs for these views (hw: host [V, 2] of
  * (height, width)). */
 size_t mvgs_dssim_workspace_size(const int32_t* hw, int32_t V);

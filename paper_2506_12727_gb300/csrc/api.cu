@@ -759,6 +759,73 @@ mvgs_status mvgs_dssim3d_loss(const float* img, const float* target, const float
     return cuda_check("dssim3d");
 }
 
+// ---- densification and Adam -------------------------------------------------
+size_t mvgs_densify_workspace_size(int64_t n) { return n < 0 ? 0 : densify_temp_bytes(n); }
+
+mvgs_status mvgs_densify(const mvgs_scene* scene, const float* accum_e1, const float* accum_e2, const float* denom,
+                         const float* normals, const mvgs_densify_params* params, int64_t capacity,
+                         float* out_means, float* out_log_scales, float* out_quats, float* out_opacity_logits,
+                         float* out_sh, int64_t* out_src, int32_t* out_kind, int64_t* n_out, void* workspace,
+                         size_t workspace_bytes, mvgs_stream stream) {
+    mvgs_status st = check_scene(scene);
+    if (st != MVGS_OK) return st;
+    if (!params || !n_out || !workspace) return fail(MVGS_EINVAL, "NULL params, n_out or workspace");
+    if (scene->n > 0 && (!accum_e1 || !accum_e2 || !denom || !normals))
+        return fail(MVGS_EINVAL, "NULL statistics or normals");
+    if (capacity < 0) return fail(MVGS_EINVAL, "capacity < 0");
+    if (capacity > 0 && (!out_means || !out_log_scales || !out_quats || !out_opacity_logits || !out_sh))
+        return fail(MVGS_EINVAL, "NULL output array");
+    if (workspace_bytes < densify_temp_bytes(scene->n))
+        return fail(MVGS_ENOSPACE, "workspace %zu < %zu bytes", workspace_bytes, densify_temp_bytes(scene->n));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DensifyArgs a;
+    a.n = scene->n;
+    a.means = scene->means;
+    a.log_scales = scene->log_scales;
+    a.quats = scene->quats;
+    a.logits = scene->opacity_logits;
+    a.sh = scene->sh;
+    a.nk = 3 * (scene->sh_degree + 1) * (scene->sh_degree + 1);
+    a.e1 = accum_e1;
+    a.e2 = accum_e2;
+    a.denom = denom;
+    a.normals = normals;
+    a.split_threshold = params->split_threshold;
+    a.clone_threshold = params->clone_threshold;
+    a.prune_logit = params->prune_logit;
+    a.log_dense_extent = params->log_dense_extent;
+    const long long* total_dev = launch_densify_plan(a, workspace, s);
+    long long total = 0;
+    if (cudaMemcpyAsync(&total, total_dev, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return cuda_check("densify count read-back");
+    *n_out = total;
+    if (total > capacity)
+        return fail(MVGS_ENOSPACE, "%lld output Gaussians exceed the capacity of %lld", total, (long long)capacity);
+    DensifyOut o{out_means, out_log_scales, out_quats, out_opacity_logits, out_sh,
+                 reinterpret_cast<long long*>(out_src), out_kind};
+    launch_densify_write(a, o, workspace, s);
+    return cuda_check("densify");
+}
+
+mvgs_status mvgs_densify_carry(int64_t n_out, const int64_t* src, const int32_t* kind, int32_t width,
+                               const float* in, float* out, mvgs_stream stream) {
+    if (n_out < 0 || width < 1) return fail(MVGS_EINVAL, "n_out < 0 or width < 1");
+    if (n_out > 0 && (!src || !kind || !in || !out)) return fail(MVGS_EINVAL, "NULL argument");
+    launch_carry(n_out, reinterpret_cast<const long long*>(src), kind, width, in, out,
+                 reinterpret_cast<cudaStream_t>(stream));
+    return cuda_check("densify carry");
+}
+
+mvgs_status mvgs_adam_step(int64_t count, float* param, const float* grad, float* m, float* v, float lr, float beta1,
+                           float beta2, float eps, int32_t step, mvgs_stream stream) {
+    if (count < 0 || step < 1) return fail(MVGS_EINVAL, "count < 0 or step < 1");
+    if (count > 0 && (!param || !grad || !m || !v)) return fail(MVGS_EINVAL, "NULL argument");
+    if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f)) return fail(MVGS_EINVAL, "betas in [0, 1)");
+    launch_adam(count, param, grad, m, v, lr, beta1, beta2, eps, step, reinterpret_cast<cudaStream_t>(stream));
+    return cuda_check("adam");
+}
+
 size_t mvgs_dssim_workspace_size(const int32_t* hw, int32_t V) {
     if (!hw || V < 1) return 0;
     return dssim_temp_bytes(hw, V);

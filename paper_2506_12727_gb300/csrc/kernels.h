@@ -64,6 +64,8 @@ void launch_adc_accumulate(const long long* rec_off, long long n, const float* g
 size_t scan_temp_bytes(uint64_t n);
 // out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
 void scan_i32_to_i64(const int* in, long long* out, uint64_t n, void* tmp, cudaStream_t s);
+// scans in[i] & mask
+void scan_masked_i32_to_i64(const int* in, int mask, long long* out, uint64_t n, void* tmp, cudaStream_t s);
 void scan_u32_to_u64(const uint32_t* in, unsigned long long* out, uint64_t n, void* tmp, cudaStream_t s);
 // gathered variant: scans in[idx[i]]
 void scan_gather_u32_to_u64(const uint32_t* in, const uint32_t* idx, unsigned long long* out, uint64_t n, void* tmp,
@@ -158,6 +160,39 @@ void launch_merge_views(const DevCam* cams, int group, unsigned long long seed, 
                         float* out_sig, cudaStream_t s);
 void launch_split_merged(const DevCam* cams, int group, unsigned long long seed, long long merged_pix,
                          const long long* mbase, int M, const float* dmerged, float* dimg, cudaStream_t s);
+
+// ---- train.cu ---------------------------------------------------------------
+struct DensifyArgs {
+    long long n;
+    const float* means;
+    const float* log_scales;
+    const float* quats;
+    const float* logits;
+    const float* sh;
+    int nk;                   // floats of SH per Gaussian
+    const float* e1;
+    const float* e2;
+    const float* denom;
+    const float* normals;     // [n, 2, 3] standard normal samples for split children
+    double split_threshold, clone_threshold, prune_logit, log_dense_extent;
+};
+struct DensifyOut {
+    float* means;
+    float* log_scales;
+    float* quats;
+    float* logits;
+    float* sh;
+    long long* src;           // or null
+    int* kind;                // or null
+};
+constexpr float kLogSplitDiv = 0.47000362924573558f;  // ln 1.6
+size_t densify_temp_bytes(long long n);
+const long long* launch_densify_plan(const DensifyArgs& a, void* tmp, cudaStream_t s);
+void launch_densify_write(const DensifyArgs& a, const DensifyOut& o, void* tmp, cudaStream_t s);
+void launch_carry(long long n_out, const long long* src, const int* kind, int width, const float* in, float* out,
+                  cudaStream_t s);
+void launch_adam(long long count, float* p, const float* g, float* m, float* v, float lr, float b1, float b2,
+                 float eps, int step, cudaStream_t s);
 
 // ---- dssim.cu --------------------------------------------------------------
 size_t dssim_temp_bytes(const int* hw, int V);

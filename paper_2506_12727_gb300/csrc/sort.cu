@@ -64,6 +64,12 @@ struct LoadDirect {
     __device__ __forceinline__ Tout operator()(uint64_t i) const { return (Tout)in[i]; }
 };
 
+struct LoadMasked {
+    const int* in;
+    int mask;
+    __device__ __forceinline__ long long operator()(uint64_t i) const { return (long long)(in[i] & mask); }
+};
+
 template <class Tout>
 struct LoadGather {
     const uint32_t* in;
@@ -535,6 +541,10 @@ size_t scan_temp_bytes(uint64_t n) { return (ceil_div_u64(n, SC_TILE) + 1) * siz
 
 void scan_i32_to_i64(const int* in, long long* out, uint64_t n, void* tmp, cudaStream_t s) {
     scan_impl(LoadDirect<int, long long>{in}, out, n, out + n, tmp, s);
+}
+
+void scan_masked_i32_to_i64(const int* in, int mask, long long* out, uint64_t n, void* tmp, cudaStream_t s) {
+    scan_impl(LoadMasked{in, mask}, out, n, out + n, tmp, s);
 }
 
 void scan_u32_to_u64(const uint32_t* in, unsigned long long* out, uint64_t n, void* tmp, cudaStream_t s) {

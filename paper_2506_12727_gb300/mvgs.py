@@ -59,6 +59,11 @@ FLAG_MASKED_PARTIAL = 1
 FLAG_DEPTH = 2
 
 
+class DensifyParams(ctypes.Structure):
+    _fields_ = [("split_threshold", ctypes.c_double), ("clone_threshold", ctypes.c_double),
+                ("prune_logit", ctypes.c_double), ("log_dense_extent", ctypes.c_double)]
+
+
 class Capacity(ctypes.Structure):
     _fields_ = [("records", ctypes.c_int64), ("keys", ctypes.c_int64)]
 
@@ -80,7 +85,8 @@ EXPORTS = ["mvgs_render_layout", "mvgs_render_views", "mvgs_render_views_backwar
            "mvgs_launch_count", "mvgs_dssim_loss_noalloc", "mvgs_last_error",
            "mvgs_partial_samples_workspace_size", "mvgs_partial_samples", "mvgs_render_views_sampled",
            "mvgs_render_views_sampled_backward", "mvgs_merge_workspace_size", "mvgs_merge_views",
-           "mvgs_split_merged_grad", "mvgs_dssim3d_workspace_size", "mvgs_dssim3d_loss"]
+           "mvgs_split_merged_grad", "mvgs_dssim3d_workspace_size", "mvgs_dssim3d_loss",
+           "mvgs_densify_workspace_size", "mvgs_densify", "mvgs_densify_carry", "mvgs_adam_step"]
 
 
 def load_library(path: str | None = None):
@@ -106,6 +112,12 @@ def load_library(path: str | None = None):
     lib.mvgs_dssim3d_workspace_size.argtypes = [P, I32]
     lib.mvgs_dssim3d_workspace_size.restype = SZ
     lib.mvgs_dssim3d_loss.argtypes = [P, P, P, P, P, I32, ctypes.c_float, P, P, P, SZ, P]
+    lib.mvgs_densify_workspace_size.argtypes = [I64]
+    lib.mvgs_densify_workspace_size.restype = SZ
+    lib.mvgs_densify.argtypes = [P, P, P, P, P, P, I64, P, P, P, P, P, P, P, P, P, SZ, P]
+    lib.mvgs_densify_carry.argtypes = [I64, P, P, I32, P, P, P]
+    lib.mvgs_adam_step.argtypes = [I64, P, P, P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                   I32, P]
     lib.mvgs_dssim_workspace_size.argtypes = [P, I32]
     lib.mvgs_dssim_workspace_size.restype = SZ
     lib.mvgs_dssim_loss.argtypes = [P, P, P, I32, ctypes.c_float, P, P, P, SZ, P]
@@ -123,7 +135,8 @@ def load_library(path: str | None = None):
     lib.mvgs_launch_count.restype = I64
     for f in ("mvgs_render_layout", "mvgs_render_views", "mvgs_render_views_backward", "mvgs_dssim_loss",
               "mvgs_adc_accumulate", "mvgs_render_views_sampled", "mvgs_render_views_sampled_backward",
-              "mvgs_partial_samples", "mvgs_merge_views", "mvgs_split_merged_grad", "mvgs_dssim3d_loss"):
+              "mvgs_partial_samples", "mvgs_merge_views", "mvgs_split_merged_grad", "mvgs_dssim3d_loss",
+              "mvgs_densify", "mvgs_densify_carry", "mvgs_adam_step"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -291,6 +304,42 @@ def dssim3d_loss(img, target, points, sigma, hw, lam, loss_per_image, dL_dimg, w
                                   hw.ctypes.data_as(ctypes.c_void_p), hw.shape[0], ctypes.c_float(lam),
                                   _ptr(loss_per_image), _ptr(dL_dimg), _ptr(workspace), workspace.numel(),
                                   _stream(stream)))
+
+
+def densify(params: dict, sh_degree: int, accum_e1, accum_e2, denom, normals, split_threshold, clone_threshold,
+            prune_logit, log_dense_extent, carry=(), stream=None):
+    """mvgs_densify (+ mvgs_densify_carry for each tensor in `carry`, e.g. Adam
+    moments shaped like a parameter).  Returns (new params, src, kind, carried)."""
+    n = int(params["means"].shape[0])
+    sc = make_scene(params, sh_degree)
+    prm = DensifyParams(float(split_threshold), float(clone_threshold), float(prune_logit), float(log_dense_extent))
+    ws = torch.empty(max(int(_lib.mvgs_densify_workspace_size(n)), 1), dtype=torch.uint8, device="cuda")
+    cap = 2 * n
+    out = {k: torch.empty((cap,) + tuple(v.shape[1:]), dtype=torch.float32, device="cuda") for k, v in params.items()}
+    src = torch.empty(max(cap, 1), dtype=torch.int64, device="cuda")
+    kind = torch.empty(max(cap, 1), dtype=torch.int32, device="cuda")
+    n_out = ctypes.c_int64(0)
+    _check(_lib.mvgs_densify(ctypes.byref(sc), _ptr(accum_e1), _ptr(accum_e2), _ptr(denom), _ptr(normals),
+                             ctypes.byref(prm), cap, _ptr(out["means"]), _ptr(out["log_scales"]), _ptr(out["quats"]),
+                             _ptr(out["opacity_logits"]), _ptr(out["sh"]), _ptr(src), _ptr(kind),
+                             ctypes.byref(n_out), _ptr(ws), ws.numel(), _stream(stream)))
+    m = int(n_out.value)
+    new = {k: v[:m].contiguous() for k, v in out.items()}
+    carried = []
+    for t in carry:
+        width = int(t[0].numel()) if t.shape[0] else 1
+        o = torch.empty((m,) + tuple(t.shape[1:]), dtype=torch.float32, device="cuda")
+        _check(_lib.mvgs_densify_carry(m, _ptr(src), _ptr(kind), width, _ptr(t.contiguous()), _ptr(o),
+                                       _stream(stream)))
+        carried.append(o)
+    return new, src[:m], kind[:m], carried
+
+
+def adam_step(param, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+    """mvgs_adam_step on one parameter tensor (in place)."""
+    _check(_lib.mvgs_adam_step(param.numel(), _ptr(param), _ptr(grad), _ptr(m), _ptr(v), ctypes.c_float(lr),
+                               ctypes.c_float(beta1), ctypes.c_float(beta2), ctypes.c_float(eps), int(step),
+                               _stream(stream)))
 
 
 def dssim_workspace_size(hw: np.ndarray) -> int:
