@@ -32,7 +32,7 @@
  *   - Every call is asynchronous on the given CUDA stream, except that
  *     mvgs_render_views synchronises the stream twice to read the number of
  *     visible (Gaussian, view) records and of duplicated keys back to the
- *     host (they size the sorts).
+ *     host (they size the sorts) -- unless MVGS_FLAG_CAPTURABLE is set.
  *   - Every call returns an mvgs_status; no exception crosses the ABI.
  *     mvgs_last_error() returns a message for the calling thread.
  *   - Float data is IEEE float32.  Images are packed per view: view v
@@ -119,6 +119,15 @@ typedef struct mvgs_config {
  * blended Gaussian; not divided by the accumulated opacity) into the state
  * array at layout.off_pixel_depth, for the 3D distance-aware D-SSIM. */
 #define MVGS_FLAG_DEPTH 2u
+/* cfg->flags bit for the forward calls: capturable mode.  The record and key
+ * counts are not read back; every launch is sized by `cap` and stops at the
+ * counts held in device memory, so the call never synchronises and can be
+ * captured in a CUDA graph (with the backward, the losses and the ADC call).
+ * `needed` gets -1s.  Results are valid only if the counts block of the state
+ * (layout.off_counts) shows needed counts within the capacity afterwards:
+ * otherwise the records and keys past it were dropped, and the caller grows
+ * the buffers and runs again. */
+#define MVGS_FLAG_CAPTURABLE 4u
 
 /* Capacities the caller sized `state` and `workspace` for:
  * records = visible (Gaussian, view) pairs, keys = (record, tile) pairs. */
@@ -132,7 +141,8 @@ typedef struct mvgs_capacity {
 typedef struct mvgs_layout {
     size_t state_bytes;
     size_t workspace_bytes;          /* forward and backward scratch (max of both) */
-    size_t off_counts;               /* int64[4]: records, keys, tiles, pixels     */
+    size_t off_counts;               /* int64[6]: records and keys held, tiles, pixels,
+                                        records and keys the batch needed          */
     size_t off_rec_offsets;          /* int64[n + 1]: records of Gaussian g are
                                         [off[g], off[g+1]) (Gaussian-major)       */
     size_t off_rec_gauss;            /* int32[records]: Gaussian index            */

@@ -127,7 +127,7 @@ struct Plan {
     // workspace offsets (forward)
     size_t w_cams = 0, w_counts = 0, w_vis = 0, w_scan = 0, w_dkeys_a = 0, w_dkeys_b = 0, w_ids_a = 0, w_ids_b = 0,
            w_order = 0, w_tiles = 0, w_tile_off = 0, w_keys_a = 0, w_keys_b = 0, w_vals_a = 0, w_vals_b = 0,
-           w_radix = 0, w_tcount = 0, w_torder = 0, w_counter = 0;
+           w_radix = 0, w_tcount = 0, w_torder = 0, w_counter = 0, w_dcount = 0;
     // workspace offsets of the sampled blend (forward and backward each carve their own)
     size_t w_chunk_off = 0, w_chunk_map = 0, w_chunk_tmp = 0, w_mask = 0;
     size_t b_chunk_off = 0, b_chunk_map = 0, b_chunk_tmp = 0, b_mask = 0;
@@ -141,7 +141,7 @@ mvgs_status check_config(const mvgs_config* cfg) {
     const int tw = cfg->tile_w, th = cfg->tile_h;
     const bool side_ok = (tw == 8 || tw == 16 || tw == 32) && (th == 8 || th == 16 || th == 32 || th == 64);
     if (!side_ok) return fail(MVGS_EINVAL, "unsupported tile %dx%d (width 8, 16 or 32; height 8 to 64)", tw, th);
-    if (cfg->flags & ~(uint32_t)(MVGS_FLAG_MASKED_PARTIAL | MVGS_FLAG_DEPTH))
+    if (cfg->flags & ~(uint32_t)(MVGS_FLAG_MASKED_PARTIAL | MVGS_FLAG_DEPTH | MVGS_FLAG_CAPTURABLE))
         return fail(MVGS_EINVAL, "unknown flags 0x%x", cfg->flags);
     const int ppt = cfg->pixels_per_thread;
     if (ppt != 0) {
@@ -243,6 +243,7 @@ mvgs_status make_plan(long long n, const mvgs_camera* cams, int V, const mvgs_co
     P.w_tcount = w.take(tile_count_temp_bytes(P.cams.data(), V, tiles));
     P.w_torder = w.take(tile_order_temp_bytes(tiles));
     P.w_counter = w.take(sizeof(int));
+    P.w_dcount = w.take(4 * sizeof(unsigned long long));
     // runs of at least 32 samples: at most one partial run per tile
     P.chunk_cap = tiles + pixels / 32 + 1;
     P.w_chunk_off = w.take((size_t)(tiles + 1) * sizeof(long long));
@@ -292,6 +293,7 @@ RecordArgs record_args(void* state, const mvgs_layout& L) {
     r.clamp = at<int>(state, L.off_rec_clamp);
     r.depth = at<float>(state, L.off_rec_depth);
     r.rect = at<short4>(state, L.off_rec_rect);
+    r.cap = 0;
     return r;
 }
 
@@ -307,11 +309,37 @@ SceneArgs scene_args(const mvgs_scene* sc) {
     return a;
 }
 
+// counts block of the state: records and keys in the arrays, tiles, pixels,
+// records and keys the batch needed (larger only after a capturable call ran
+// out of capacity)
 __global__ void set_counts_kernel(long long* c, long long R, long long K, long long T, long long P) {
     c[0] = R;
     c[1] = K;
     c[2] = T;
     c[3] = P;
+    c[4] = R;
+    c[5] = K;
+}
+
+// capturable mode: the counts stay on the device
+__global__ void clamp_records_kernel(const long long* rec_total, long long cap, unsigned long long* dcnt) {
+    const long long R = *rec_total;
+    dcnt[0] = (unsigned long long)(R < cap ? R : cap);
+}
+
+__global__ void clamp_keys_kernel(long long cap, unsigned long long* dcnt) {
+    const unsigned long long K = dcnt[1];
+    dcnt[2] = K < (unsigned long long)cap ? K : (unsigned long long)cap;
+}
+
+__global__ void set_counts_dev_kernel(long long* c, const long long* rec_total, const unsigned long long* dcnt,
+                                      long long T, long long P) {
+    c[0] = (long long)dcnt[0];
+    c[1] = (long long)dcnt[2];
+    c[2] = T;
+    c[3] = P;
+    c[4] = *rec_total;
+    c[5] = (long long)dcnt[1];
 }
 
 int bits_for(long long tiles) {
@@ -443,17 +471,36 @@ static mvgs_status render_impl(const mvgs_scene* scene, const mvgs_camera* cams,
         StageTimer t(MVGS_STAGE_SCAN_RECORDS, s);
         scan_i32_to_i64(counts, rec.rec_off, (uint64_t)n, at<void>(workspace, P.w_scan), s);
     }
+    // Without MVGS_FLAG_CAPTURABLE the record and key counts are read back to
+    // size the sorts exactly; with it they stay on the device and every
+    // launch is sized by the capacity (the kernels stop at the device count),
+    // so the call can be captured in a CUDA graph.
+    const bool capt = (cfg->flags & MVGS_FLAG_CAPTURABLE) != 0;
+    unsigned long long* dcnt = at<unsigned long long>(workspace, P.w_dcount);
     long long R = 0;
-    if (cudaMemcpyAsync(&R, rec.rec_off + n, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-        return cuda_check("record count read-back");
-    if ((st = cuda_check("participation")) != MVGS_OK) return st;
-    if (needed) {
-        needed->records = R;
-        needed->keys = 0;
+    if (!capt) {
+        if (cudaMemcpyAsync(&R, rec.rec_off + n, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return cuda_check("record count read-back");
+        if ((st = cuda_check("participation")) != MVGS_OK) return st;
+        if (needed) {
+            needed->records = R;
+            needed->keys = 0;
+        }
+        if (R > cap->records)
+            return fail(MVGS_ENOSPACE, "%lld visible records exceed the capacity of %lld", R,
+                        (long long)cap->records);
+        rec.cap = R;
+    } else {
+        clamp_records_kernel<<<1, 1, 0, s>>>(rec.rec_off + n, cap->records, dcnt);
+        note_launches(1);
+        rec.cap = cap->records;
+        if (needed) {
+            needed->records = -1;  // on the device: counts block of the state
+            needed->keys = -1;
+        }
     }
-    if (R > cap->records)
-        return fail(MVGS_ENOSPACE, "%lld visible records exceed the capacity of %lld", R, (long long)cap->records);
+    const Count Rc = capt ? Count((unsigned long long)cap->records, dcnt) : Count((unsigned long long)R);
 
     // projection, colour, radius and tile rectangle of every record
     uint32_t* dkeys_a = at<uint32_t>(workspace, P.w_dkeys_a);
@@ -469,27 +516,34 @@ static mvgs_status render_impl(const mvgs_scene* scene, const mvgs_camera* cams,
     {
         StageTimer t(MVGS_STAGE_DEPTH_SORT, s);
         radix_sort_pairs(dkeys_a, ids_a, at<uint32_t>(workspace, P.w_dkeys_b), at<uint32_t>(workspace, P.w_ids_b),
-                         order, (uint64_t)R, 32, at<void>(workspace, P.w_radix), s);
+                         order, Rc, 32, at<void>(workspace, P.w_radix), s);
     }
     unsigned long long* tile_off = at<unsigned long long>(workspace, P.w_tile_off);
     {
         StageTimer t(MVGS_STAGE_SCAN_TILES, s);
-        scan_gather_u32_to_u64(tiles, order, tile_off, (uint64_t)R, at<void>(workspace, P.w_scan), s);
+        scan_gather_u32_to_u64(tiles, order, tile_off, Rc, capt ? dcnt + 1 : nullptr, at<void>(workspace, P.w_scan),
+                               s);
     }
     unsigned long long K = 0;
-    if (cudaMemcpyAsync(&K, tile_off + R, sizeof(K), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-        return cuda_check("key count read-back");
-    if ((st = cuda_check("preprocess")) != MVGS_OK) return st;
-    if (needed) needed->keys = (long long)K;
-    if (K >= (1ULL << 32)) return fail(MVGS_EOVERFLOW, "%llu keys do not fit 32-bit positions", K);
-    if ((long long)K > cap->keys)
-        return fail(MVGS_ENOSPACE, "%llu keys exceed the capacity of %lld", K, (long long)cap->keys);
+    if (!capt) {
+        if (cudaMemcpyAsync(&K, tile_off + R, sizeof(K), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return cuda_check("key count read-back");
+        if ((st = cuda_check("preprocess")) != MVGS_OK) return st;
+        if (needed) needed->keys = (long long)K;
+        if (K >= (1ULL << 32)) return fail(MVGS_EOVERFLOW, "%llu keys do not fit 32-bit positions", K);
+        if ((long long)K > cap->keys)
+            return fail(MVGS_ENOSPACE, "%llu keys exceed the capacity of %lld", K, (long long)cap->keys);
+    } else {
+        clamp_keys_kernel<<<1, 1, 0, s>>>(cap->keys, dcnt);
+        note_launches(1);
+    }
+    const Count Kc = capt ? Count((unsigned long long)cap->keys, dcnt + 2) : Count(K);
 
     uint32_t* sorted = at<uint32_t>(state, L.off_sorted_records);
     {
         StageTimer t(MVGS_STAGE_TILE_SORT, s);
-        tile_sort(order, tile_off, (uint64_t)R, K, rec.rect, rec.rec_v, dcams, P.tiles, bits_for(P.tiles),
+        tile_sort(order, tile_off, Rc, Kc, rec.rect, rec.rec_v, dcams, P.tiles, bits_for(P.tiles),
                   at<uint32_t>(workspace, P.w_keys_a), at<uint32_t>(workspace, P.w_vals_a),
                   at<uint32_t>(workspace, P.w_keys_b), at<uint32_t>(workspace, P.w_vals_b), sorted,
                   at<void>(workspace, P.w_radix), s);
@@ -497,11 +551,14 @@ static mvgs_status render_impl(const mvgs_scene* scene, const mvgs_camera* cams,
     long long* ranges = at<long long>(state, L.off_tile_ranges);
     {
         StageTimer t(MVGS_STAGE_RANGES, s);
-        tile_ranges_from_rects(rec.rect, rec.rec_v, (uint64_t)R, dcams, P.cams.data(), V, P.tiles, ranges,
+        tile_ranges_from_rects(rec.rect, rec.rec_v, Rc, Kc, dcams, P.cams.data(), V, P.tiles, ranges,
                                at<void>(workspace, P.w_tcount), s);
         tile_order(ranges, P.tiles, at<uint32_t>(state, L.off_tile_order), at<void>(workspace, P.w_torder), s);
     }
-    set_counts_kernel<<<1, 1, 0, s>>>(counts_dev, R, (long long)K, P.tiles, P.pixels);
+    if (capt)
+        set_counts_dev_kernel<<<1, 1, 0, s>>>(counts_dev, rec.rec_off + n, dcnt, P.tiles, P.pixels);
+    else
+        set_counts_kernel<<<1, 1, 0, s>>>(counts_dev, R, (long long)K, P.tiles, P.pixels);
     note_launches(1);
 
     BlendArgs ba;
@@ -554,7 +611,8 @@ static mvgs_status backward_impl(const mvgs_scene* scene, const mvgs_camera* cam
     DevCam* dcams = at<DevCam>(workspace, P.b_cams);
     upload_cams(P.cams.data(), V, dcams, s);
     void* st_mut = const_cast<void*>(state);  // read only below; RecordArgs carries non-const pointers
-    const RecordArgs rec = record_args(st_mut, L);
+    RecordArgs rec = record_args(st_mut, L);
+    rec.cap = cap->records;
     float* rec_grad = at<float>(workspace, P.b_grad);
     double* rec_conic = reinterpret_cast<double*>(rec_grad + (size_t)cap->records * kGradStride);
     {
@@ -857,7 +915,7 @@ mvgs_status mvgs_adc_accumulate(const void* state, int64_t n, const float* g_mea
     const long long* rec_off = at<long long>(state, 256);
     {
         StageTimer t(MVGS_STAGE_ADC, reinterpret_cast<cudaStream_t>(stream));
-        launch_adc_accumulate(rec_off, n, g_mean2d, e1, accum_e1, accum_e2, denom,
+        launch_adc_accumulate(rec_off, at<long long>(state, 0), n, g_mean2d, e1, accum_e1, accum_e2, denom,
                               reinterpret_cast<cudaStream_t>(stream));
     }
     return cuda_check("adc");

@@ -35,6 +35,20 @@ struct __align__(16) DevCam {
 };
 static_assert(sizeof(DevCam) == 128, "camera table entry is 128 bytes");
 
+// An element count: known on the host (max), or -- in the capturable mode,
+// where no count is read back -- held in device memory and bounded by the
+// capacity the buffers were sized for: min(max, *dev).
+struct Count {
+    unsigned long long max;
+    const unsigned long long* dev;
+    __host__ __device__ Count(unsigned long long m = 0, const unsigned long long* d = nullptr) : max(m), dev(d) {}
+    __device__ __forceinline__ unsigned long long get() const {
+        if (!dev) return max;
+        const unsigned long long v = *dev;
+        return v < max ? v : max;
+    }
+};
+
 constexpr int kCamChunk = 32;
 struct CamChunk {
     DevCam c[kCamChunk];

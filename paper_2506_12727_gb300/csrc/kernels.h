@@ -39,6 +39,7 @@ struct RecordArgs {
     int* clamp;
     float* depth;
     short4* rect;
+    long long cap;       // records the arrays hold: no record index reaches it
 };
 
 // vis: [n * V] bytes, 1 where (g, v) is visible; counts: visible views per Gaussian.
@@ -57,8 +58,9 @@ void launch_preprocess_backward(const SceneArgs& sc, const DevCam* cams, int V, 
                                 const float* rec_grad, const double* rec_conic, float* g_means,
                                 float* g_log_scales, float* g_quats, float* g_logits, float* g_sh,
                                 float* out_mean2d, float* out_e1, cudaStream_t s);
-void launch_adc_accumulate(const long long* rec_off, long long n, const float* g_mean2d, const float* e1,
-                           float* accum_e1, float* accum_e2, float* denom, cudaStream_t s);
+// records at or past *rec_count are ignored
+void launch_adc_accumulate(const long long* rec_off, const long long* rec_count, long long n, const float* g_mean2d,
+                           const float* e1, float* accum_e1, float* accum_e2, float* denom, cudaStream_t s);
 
 // ---- sort.cu ---------------------------------------------------------------
 size_t scan_temp_bytes(uint64_t n);
@@ -68,8 +70,9 @@ void scan_i32_to_i64(const int* in, long long* out, uint64_t n, void* tmp, cudaS
 void scan_masked_i32_to_i64(const int* in, int mask, long long* out, uint64_t n, void* tmp, cudaStream_t s);
 void scan_u32_to_u64(const uint32_t* in, unsigned long long* out, uint64_t n, void* tmp, cudaStream_t s);
 // gathered variant: scans in[idx[i]]
-void scan_gather_u32_to_u64(const uint32_t* in, const uint32_t* idx, unsigned long long* out, uint64_t n, void* tmp,
-                            cudaStream_t s);
+// (also the total into *total when given; n may be a device count)
+void scan_gather_u32_to_u64(const uint32_t* in, const uint32_t* idx, unsigned long long* out, Count n,
+                            unsigned long long* total, void* tmp, cudaStream_t s);
 
 size_t radix_temp_bytes(uint64_t n);
 size_t tile_sort_temp_bytes(uint64_t K);
@@ -77,14 +80,14 @@ size_t tile_sort_temp_bytes(uint64_t K);
 // (keys_a, vals_a), which are overwritten; buffers _b are scratch; the sorted
 // values end in vals_out.
 void radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b, uint32_t* vals_out,
-                      uint64_t n, int bits, void* tmp, cudaStream_t s);
+                      Count n, int bits, void* tmp, cudaStream_t s);
 
 // Stable sort, by global (view, tile) id, of one entry per (record, covered
 // tile) taken in the order of `order` (records sorted by depth); tile_off is
 // the exclusive scan of the records' tile counts in that order.  The entries
 // are generated inside the first radix pass.  Sorted record ids end in
 // vals_out; keys_a/b and vals_a/b are scratch of K entries.
-void tile_sort(const uint32_t* order, const unsigned long long* tile_off, uint64_t R, uint64_t K, const short4* rect,
+void tile_sort(const uint32_t* order, const unsigned long long* tile_off, Count R, Count K, const short4* rect,
                const int* rec_v, const DevCam* cams, long long tiles, int bits, uint32_t* keys_a, uint32_t* vals_a,
                uint32_t* keys_b, uint32_t* vals_b, uint32_t* vals_out, void* tmp, cudaStream_t s);
 
@@ -94,7 +97,7 @@ void tile_order(const long long* ranges, long long tiles, uint32_t* order, void*
 
 // Per-tile [start, end) of the sorted list, from the records' rectangles.
 size_t tile_count_temp_bytes(const DevCam* host_cams, int V, long long tiles);
-void tile_ranges_from_rects(const short4* rect, const int* rec_v, uint64_t R, const DevCam* cams,
+void tile_ranges_from_rects(const short4* rect, const int* rec_v, Count R, Count K, const DevCam* cams,
                             const DevCam* host_cams, int V, long long tiles, long long* ranges, void* tmp,
                             cudaStream_t s);
 

@@ -272,6 +272,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneArgs sc, const Dev
     const float* shg = sc.sh + (size_t)g * NK * 3;
     for (int v = 0; v < V; v++) {
         if (!vis[g * V + v]) continue;
+        if (r >= rec.cap) break;  // capturable mode past its record capacity (reported through the counts)
         const DevCam& cam = cams[v];
         Proj P;
         const bool ok = project(G, cam, tw, th, P);
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(128) preprocess_backward_kernel(SceneArgs sc, 
     float gsh[NK * 3];
 #pragma unroll
     for (int i = 0; i < NK * 3; i++) gsh[i] = 0.f;
-    const long long r0 = rec.rec_off[g], r1 = rec.rec_off[g + 1];
+    const long long r0 = rec.rec_off[g], r1 = min(rec.rec_off[g + 1], rec.cap);
     for (long long r = r0; r < r1; r++) {
         const DevCam& cam = cams[rec.rec_v[r]];
         Proj P;
@@ -480,12 +481,13 @@ __global__ void __launch_bounds__(128) preprocess_backward_kernel(SceneArgs sc, 
 
 // E_1 (norm per pixel, then add) and E_2 (add per view, then norm) of
 // Sec. 5.2.2, accumulated over calls; one thread per Gaussian.
-__global__ void adc_kernel(const long long* __restrict__ rec_off, long long n, const float* __restrict__ g_mean2d,
-                           const float* __restrict__ e1, float* __restrict__ acc_e1, float* __restrict__ acc_e2,
-                           float* __restrict__ denom) {
+__global__ void adc_kernel(const long long* __restrict__ rec_off, const long long* __restrict__ rec_count, long long n,
+                           const float* __restrict__ g_mean2d, const float* __restrict__ e1,
+                           float* __restrict__ acc_e1, float* __restrict__ acc_e2, float* __restrict__ denom) {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
-    const long long r0 = rec_off[g], r1 = rec_off[g + 1];
+    const long long rc = *rec_count;
+    const long long r0 = min(rec_off[g], rc), r1 = min(rec_off[g + 1], rc);
     float s1 = 0.f, s2 = 0.f;
     for (long long r = r0; r < r1; r++) {
         const float2 m = *reinterpret_cast<const float2*>(g_mean2d + 2 * r);
@@ -565,10 +567,10 @@ void launch_preprocess_backward(const SceneArgs& sc, const DevCam* cams, int V, 
 #undef MVGS_PB
 }
 
-void launch_adc_accumulate(const long long* rec_off, long long n, const float* g_mean2d, const float* e1,
-                           float* accum_e1, float* accum_e2, float* denom, cudaStream_t s) {
+void launch_adc_accumulate(const long long* rec_off, const long long* rec_count, long long n, const float* g_mean2d,
+                           const float* e1, float* accum_e1, float* accum_e2, float* denom, cudaStream_t s) {
     if (n == 0) return;
-    adc_kernel<<<blocks_for(n, 256), 256, 0, s>>>(rec_off, n, g_mean2d, e1, accum_e1, accum_e2, denom);
+    adc_kernel<<<blocks_for(n, 256), 256, 0, s>>>(rec_off, rec_count, n, g_mean2d, e1, accum_e1, accum_e2, denom);
     note_launches(1);
 }
 

@@ -78,8 +78,9 @@ struct LoadGather {
 };
 
 template <class Load, class T>
-__global__ void __launch_bounds__(SC_THREADS) scan_reduce_kernel(Load ld, uint64_t n, T* partials) {
+__global__ void __launch_bounds__(SC_THREADS) scan_reduce_kernel(Load ld, Count cn, T* partials) {
     __shared__ T buf[33];
+    const uint64_t n = cn.get();
     const uint64_t base = (uint64_t)blockIdx.x * SC_TILE;
     T s = 0;
 #pragma unroll 4
@@ -93,7 +94,8 @@ __global__ void __launch_bounds__(SC_THREADS) scan_reduce_kernel(Load ld, uint64
 }
 
 template <class T>
-__global__ void __launch_bounds__(SPINE_THREADS) scan_spine_kernel(T* partials, uint64_t nb, T* total_out) {
+__global__ void __launch_bounds__(SPINE_THREADS) scan_spine_kernel(T* partials, uint64_t nb, T* total_out,
+                                                                   T* end_out, Count cn) {
     __shared__ T buf[33];
     T carry = 0;
     for (uint64_t start = 0; start < nb; start += SPINE_THREADS) {
@@ -105,14 +107,16 @@ __global__ void __launch_bounds__(SPINE_THREADS) scan_spine_kernel(T* partials, 
         carry += tot;
     }
     if (threadIdx.x == 0 && total_out) *total_out = carry;
+    if (threadIdx.x == 0 && end_out) end_out[cn.get()] = carry;
 }
 
 __device__ __forceinline__ int pad_index(int i) { return i + (i >> 5); }
 
 template <class Load, class T>
-__global__ void __launch_bounds__(SC_THREADS) scan_down_kernel(Load ld, uint64_t n, const T* partials, T* out) {
+__global__ void __launch_bounds__(SC_THREADS) scan_down_kernel(Load ld, Count cn, const T* partials, T* out) {
     __shared__ T tile[SC_TILE + SC_TILE / 32];
     __shared__ T buf[33];
+    const uint64_t n = cn.get();
     const uint64_t base = (uint64_t)blockIdx.x * SC_TILE;
     for (int i = threadIdx.x; i < SC_TILE; i += SC_THREADS) {
         const uint64_t idx = base + i;
@@ -142,16 +146,19 @@ __global__ void __launch_bounds__(SC_THREADS) scan_down_kernel(Load ld, uint64_t
 
 uint64_t ceil_div_u64(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 
+// Exclusive scan of ld(0 .. n); the total goes to out[n] when write_end, and
+// to *total_out when given.
 template <class Load, class T>
-void scan_impl(Load ld, T* out, uint64_t n, T* total_out, void* tmp, cudaStream_t s) {
-    if (n == 0) {
+void scan_impl(Load ld, T* out, Count n, bool write_end, T* total_out, void* tmp, cudaStream_t s) {
+    if (n.max == 0) {
         if (total_out) cudaMemsetAsync(total_out, 0, sizeof(T), s);
+        if (write_end) cudaMemsetAsync(out, 0, sizeof(T), s);
         return;
     }
-    const uint64_t nb = ceil_div_u64(n, SC_TILE);
+    const uint64_t nb = ceil_div_u64(n.max, SC_TILE);
     T* partials = static_cast<T*>(tmp);
     scan_reduce_kernel<Load, T><<<(unsigned)nb, SC_THREADS, 0, s>>>(ld, n, partials);
-    scan_spine_kernel<T><<<1, SPINE_THREADS, 0, s>>>(partials, nb, total_out);
+    scan_spine_kernel<T><<<1, SPINE_THREADS, 0, s>>>(partials, nb, total_out, write_end ? out : nullptr, n);
     scan_down_kernel<Load, T><<<(unsigned)nb, SC_THREADS, 0, s>>>(ld, n, partials, out);
     note_launches(3);
 }
@@ -251,9 +258,10 @@ __device__ __forceinline__ void rank_and_scatter(RankSmem& sm, const uint32_t (&
 
 // Per-block digit histogram, stored digit-major so that one exclusive scan of
 // the whole table gives every block's first output position per digit.
-__global__ void __launch_bounds__(RS_THREADS) rs_upsweep(const uint32_t* __restrict__ keys, uint64_t n, int shift,
+__global__ void __launch_bounds__(RS_THREADS) rs_upsweep(const uint32_t* __restrict__ keys, Count cn, int shift,
                                                         uint32_t* __restrict__ counts, uint32_t nblocks) {
     __shared__ uint32_t hist[RS_WARPS * 256];
+    const uint64_t n = cn.get();
     for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) hist[i] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -274,11 +282,13 @@ template <bool WRITE_KEYS>
 __global__ void __launch_bounds__(RS_THREADS, 2) rs_downsweep(const uint32_t* __restrict__ kin,
                                                              const uint32_t* __restrict__ vin,
                                                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                                             uint64_t n, int shift,
+                                                             Count cn, int shift,
                                                              const uint32_t* __restrict__ offsets, uint32_t nblocks) {
     __shared__ RankSmem sm;
+    const uint64_t n = cn.get();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t block0 = (uint64_t)blockIdx.x * RS_TILE;
+    if (block0 >= n) return;  // a block past the keys (capturable mode)
     const uint64_t base = block0 + warp * RS_SEG + lane;
     uint32_t k[RS_ITEMS];
 #pragma unroll
@@ -300,7 +310,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) rs_downsweep(const uint32_t* __
 struct DupSrc {
     const uint32_t* order;             // records by depth
     const unsigned long long* off;     // [R + 1] exclusive scan of tiles in that order
-    uint64_t R;
+    Count R;
     const short4* rect;
     const int* rec_v;
     const DevCam* cams;
@@ -321,7 +331,7 @@ __device__ __forceinline__ uint64_t dup_record(const DupSrc& src, const int* s_o
         }
         return rlo + lo;
     }
-    uint64_t lo = 0, hi = src.R - 1;
+    uint64_t lo = 0, hi = src.R.get() - 1;
     while (lo < hi) {
         const uint64_t mid = (lo + hi + 1) >> 1;
         if (src.off[mid] <= k) lo = mid; else hi = mid - 1;
@@ -333,11 +343,15 @@ constexpr int DUP_ITEMS = RS_ITEMS;  // consecutive entries per thread
 
 // first[b] = the record holding entry b * TILE, for every radix block b:
 // each record fills the blocks whose first entry it holds, so no block has to
-// search for its records.  first[nblocks] = R - 1.
-__global__ void block_starts_kernel(const unsigned long long* __restrict__ off, uint64_t R, uint32_t nblocks,
+// search for its records; the block after the last entry gets R - 1.
+__global__ void block_starts_kernel(const unsigned long long* __restrict__ off, Count Rc, uint32_t nblocks,
                                     uint32_t* __restrict__ first) {
+    const uint64_t R = Rc.get();
     const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r == 0) first[nblocks] = (uint32_t)(R - 1);
+    if (r == 0) {
+        const uint64_t end = (off[R] + RS_TILE - 1) / RS_TILE;
+        first[end < nblocks ? end : nblocks] = (uint32_t)(R - 1);
+    }
     if (r >= R) return;
     const uint64_t b0 = (off[r] + RS_TILE - 1) / RS_TILE;
     const uint64_t b1 = (off[r + 1] + RS_TILE - 1) / RS_TILE;  // exclusive
@@ -345,13 +359,18 @@ __global__ void block_starts_kernel(const unsigned long long* __restrict__ off, 
 }
 
 __global__ void __launch_bounds__(RS_THREADS) dup_hist_kernel(DupSrc src, const uint32_t* __restrict__ first_rec,
-                                                             uint64_t K, uint32_t* __restrict__ keys,
+                                                             Count Kc, uint32_t* __restrict__ keys,
                                                              uint32_t* __restrict__ vals,
                                                              uint32_t* __restrict__ counts, uint32_t nblocks) {
     __shared__ uint32_t hist[RS_WARPS * 256];
     __shared__ int s_off[RS_TILE + 2];
-    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) hist[i] = 0;
+    const uint64_t K = Kc.get();
     const uint64_t k0 = (uint64_t)blockIdx.x * RS_TILE;
+    if (k0 >= K) {  // a block past the entries (capturable mode): empty histogram
+        counts[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = 0u;
+        return;
+    }
+    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) hist[i] = 0;
     // records [rlo, rlo + nr) hold this block's entries (the next block's
     // first record may start inside it); a record without tiles shares its
     // offset with the next, so they can outnumber the entries: then search
@@ -428,10 +447,10 @@ __global__ void __launch_bounds__(RS_THREADS) dup_hist_kernel(DupSrc src, const 
 // per-tile list lengths from the records' rectangles (2D difference counts),
 // so the tile ranges need no pass over the sorted keys
 // ---------------------------------------------------------------------------
-__global__ void rect_diff_kernel(const short4* __restrict__ rect, const int* __restrict__ rec_v, uint64_t R,
+__global__ void rect_diff_kernel(const short4* __restrict__ rect, const int* __restrict__ rec_v, Count Rc,
                                  const DevCam* __restrict__ cams, int* __restrict__ diff) {
     const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= R) return;
+    if (r >= Rc.get()) return;
     const short4 rc = rect[r];
     if (rc.z <= rc.x || rc.w <= rc.y) return;
     const DevCam& cam = cams[rec_v[r]];
@@ -454,9 +473,10 @@ constexpr int RD_THREADS = 512;
 constexpr long long RD_MAX_CELLS = 54 * 1024;  // 216 KB of int counters
 
 __global__ void __launch_bounds__(RD_THREADS)
-rect_diff_smem_kernel(const short4* __restrict__ rect, const int* __restrict__ rec_v, uint64_t R,
+rect_diff_smem_kernel(const short4* __restrict__ rect, const int* __restrict__ rec_v, Count Rc,
                       const DevCam* __restrict__ cams, int cells, int* __restrict__ parts) {
     extern __shared__ int grid[];
+    const uint64_t R = Rc.get();
     for (int c = threadIdx.x; c < cells; c += blockDim.x) grid[c] = 0;
     __syncthreads();
     const uint64_t chunk = (R + gridDim.x - 1) / gridDim.x;
@@ -524,12 +544,15 @@ __global__ void tile_order_keys_kernel(const long long* __restrict__ ranges, lon
     ids[t] = (uint32_t)t;
 }
 
-__global__ void ranges_kernel(const unsigned long long* __restrict__ starts, long long tiles,
+// Ranges are clamped to the entries that were generated (all of them unless
+// a capturable call ran out of key capacity).
+__global__ void ranges_kernel(const unsigned long long* __restrict__ starts, long long tiles, Count Kc,
                               long long* __restrict__ ranges) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= tiles) return;
-    ranges[2 * t] = (long long)starts[t];
-    ranges[2 * t + 1] = (long long)starts[t + 1];
+    const unsigned long long K = Kc.get();
+    ranges[2 * t] = (long long)(starts[t] < K ? starts[t] : K);
+    ranges[2 * t + 1] = (long long)(starts[t + 1] < K ? starts[t + 1] : K);
 }
 
 }  // namespace
@@ -540,20 +563,20 @@ __global__ void ranges_kernel(const unsigned long long* __restrict__ starts, lon
 size_t scan_temp_bytes(uint64_t n) { return (ceil_div_u64(n, SC_TILE) + 1) * sizeof(unsigned long long); }
 
 void scan_i32_to_i64(const int* in, long long* out, uint64_t n, void* tmp, cudaStream_t s) {
-    scan_impl(LoadDirect<int, long long>{in}, out, n, out + n, tmp, s);
+    scan_impl(LoadDirect<int, long long>{in}, out, n, true, (long long*)nullptr, tmp, s);
 }
 
 void scan_masked_i32_to_i64(const int* in, int mask, long long* out, uint64_t n, void* tmp, cudaStream_t s) {
-    scan_impl(LoadMasked{in, mask}, out, n, out + n, tmp, s);
+    scan_impl(LoadMasked{in, mask}, out, n, true, (long long*)nullptr, tmp, s);
 }
 
 void scan_u32_to_u64(const uint32_t* in, unsigned long long* out, uint64_t n, void* tmp, cudaStream_t s) {
-    scan_impl(LoadDirect<uint32_t, unsigned long long>{in}, out, n, out + n, tmp, s);
+    scan_impl(LoadDirect<uint32_t, unsigned long long>{in}, out, n, true, (unsigned long long*)nullptr, tmp, s);
 }
 
-void scan_gather_u32_to_u64(const uint32_t* in, const uint32_t* idx, unsigned long long* out, uint64_t n, void* tmp,
-                            cudaStream_t s) {
-    scan_impl(LoadGather<unsigned long long>{in, idx}, out, n, out + n, tmp, s);
+void scan_gather_u32_to_u64(const uint32_t* in, const uint32_t* idx, unsigned long long* out, Count n,
+                            unsigned long long* total, void* tmp, cudaStream_t s) {
+    scan_impl(LoadGather<unsigned long long>{in, idx}, out, n, true, total, tmp, s);
 }
 
 static uint64_t radix_blocks(uint64_t n) { return ceil_div_u64(n, RS_TILE); }
@@ -576,18 +599,18 @@ void radix_pass(uint64_t n, void* tmp, cudaStream_t s, Up up, Down down) {
     uint32_t* counts = static_cast<uint32_t*>(tmp);
     void* scan_tmp = static_cast<char*>(tmp) + ((256 * nb * sizeof(uint32_t)) + 255) / 256 * 256;
     up((unsigned)nb, counts);
-    scan_impl(LoadDirect<uint32_t, uint32_t>{counts}, counts, 256 * nb, (uint32_t*)nullptr, scan_tmp, s);
+    scan_impl(LoadDirect<uint32_t, uint32_t>{counts}, counts, Count(256 * nb), false, (uint32_t*)nullptr, scan_tmp, s);
     down((unsigned)nb, counts);
     note_launches(2);
 }
 }  // namespace
 
 void radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b, uint32_t* vals_out,
-                      uint64_t n, int bits, void* tmp, cudaStream_t s) {
-    if (n == 0) return;
+                      Count n, int bits, void* tmp, cudaStream_t s) {
+    if (n.max == 0) return;
     const int passes = (bits + 7) / 8;
     if (passes == 0) {
-        cudaMemcpyAsync(vals_out, vals_a, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(vals_out, vals_a, n.max * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
         return;
     }
     uint32_t *kin = keys_a, *vin = vals_a, *kout = keys_b, *vout = vals_b;
@@ -596,7 +619,7 @@ void radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint
         if (last) vout = vals_out;
         const int shift = 8 * p;
         radix_pass(
-            n, tmp, s,
+            n.max, tmp, s,
             [&](unsigned nb, uint32_t* counts) { rs_upsweep<<<nb, RS_THREADS, 0, s>>>(kin, n, shift, counts, nb); },
             [&](unsigned nb, uint32_t* counts) {
                 if (last) rs_downsweep<false><<<nb, RS_THREADS, 0, s>>>(kin, vin, kout, vout, n, shift, counts, nb);
@@ -611,12 +634,12 @@ void radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint
     }
 }
 
-void tile_sort(const uint32_t* order, const unsigned long long* tile_off, uint64_t R, uint64_t K, const short4* rect,
+void tile_sort(const uint32_t* order, const unsigned long long* tile_off, Count R, Count K, const short4* rect,
                const int* rec_v, const DevCam* cams, long long tiles, int bits, uint32_t* keys_a, uint32_t* vals_a,
                uint32_t* keys_b, uint32_t* vals_b, uint32_t* vals_out, void* tmp, cudaStream_t s) {
-    if (K == 0 || R == 0) return;
+    if (K.max == 0 || R.max == 0) return;
     // the radix pass uses the front of tmp; the block starts go behind it
-    uint32_t* first_rec = reinterpret_cast<uint32_t*>(static_cast<char*>(tmp) + radix_temp_bytes(K));
+    uint32_t* first_rec = reinterpret_cast<uint32_t*>(static_cast<char*>(tmp) + radix_temp_bytes(K.max));
     const DupSrc src{order, tile_off, R, rect, rec_v, cams, (uint32_t)tiles};
     const int passes = bits > 8 ? (bits + 7) / 8 : 1;
     uint32_t *kin = keys_a, *vin = vals_a, *kout = keys_b, *vout = vals_b;
@@ -625,11 +648,11 @@ void tile_sort(const uint32_t* order, const unsigned long long* tile_off, uint64
         if (last) vout = vals_out;
         const int shift = 8 * p;
         radix_pass(
-            K, tmp, s,
+            K.max, tmp, s,
             [&](unsigned nb, uint32_t* counts) {
                 // pass 0 writes the entries and the histogram of their first digit
                 if (p == 0) {
-                    block_starts_kernel<<<(unsigned)ceil_div_u64(R, 256), 256, 0, s>>>(tile_off, R, nb, first_rec);
+                    block_starts_kernel<<<(unsigned)ceil_div_u64(R.max, 256), 256, 0, s>>>(tile_off, R, nb, first_rec);
                     dup_hist_kernel<<<nb, RS_THREADS, 0, s>>>(src, first_rec, K, keys_a, vals_a, counts, nb);
                     note_launches(1);
                 } else {
@@ -682,7 +705,7 @@ size_t tile_count_temp_bytes(const DevCam* host_cams, int V, long long tiles) {
     return a + b + c + d + scan_temp_bytes((uint64_t)tiles);
 }
 
-void tile_ranges_from_rects(const short4* rect, const int* rec_v, uint64_t R, const DevCam* cams,
+void tile_ranges_from_rects(const short4* rect, const int* rec_v, Count R, Count K, const DevCam* cams,
                             const DevCam* host_cams, int V, long long tiles, long long* ranges, void* tmp,
                             cudaStream_t s) {
     const long long cells = diff_cells(host_cams, V);
@@ -698,21 +721,30 @@ void tile_ranges_from_rects(const short4* rect, const int* rec_v, uint64_t R, co
         int* parts = reinterpret_cast<int*>(base);
         base += (size_t)RD_PARTS * a;
         const size_t smem = (size_t)cells * sizeof(int);
-        cudaFuncSetAttribute(rect_diff_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // raise the kernel's shared-memory limit once per device, to the
+        // largest size used (not at every call: the call may be captured)
+        static thread_local int raised[64] = {0};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev < 64 && raised[dev] < (int)(RD_MAX_CELLS * sizeof(int))) {
+            cudaFuncSetAttribute(rect_diff_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(RD_MAX_CELLS * sizeof(int)));
+            raised[dev] = (int)(RD_MAX_CELLS * sizeof(int));
+        }
         rect_diff_smem_kernel<<<RD_PARTS, RD_THREADS, smem, s>>>(rect, rec_v, R, cams, (int)cells, parts);
         sum_parts_kernel<<<(unsigned)ceil_div_u64((uint64_t)cells, 256), 256, 0, s>>>(parts, (int)cells, RD_PARTS,
                                                                                        diff);
         note_launches(2);
     } else {
         cudaMemsetAsync(diff, 0, (size_t)cells * sizeof(int), s);
-        if (R > 0) {
-            rect_diff_kernel<<<(unsigned)ceil_div_u64(R, 256), 256, 0, s>>>(rect, rec_v, R, cams, diff);
+        if (R.max > 0) {
+            rect_diff_kernel<<<(unsigned)ceil_div_u64(R.max, 256), 256, 0, s>>>(rect, rec_v, R, cams, diff);
             note_launches(1);
         }
     }
     diff_to_counts_kernel<<<V, 256, 0, s>>>(cams, diff, counts);
     scan_u32_to_u64(counts, starts, (uint64_t)tiles, base, s);
-    ranges_kernel<<<(unsigned)ceil_div_u64((uint64_t)tiles, 256), 256, 0, s>>>(starts, tiles, ranges);
+    ranges_kernel<<<(unsigned)ceil_div_u64((uint64_t)tiles, 256), 256, 0, s>>>(starts, tiles, K, ranges);
     note_launches(2);
 }
 

@@ -57,6 +57,7 @@ class Samples(ctypes.Structure):
 
 FLAG_MASKED_PARTIAL = 1
 FLAG_DEPTH = 2
+FLAG_CAPTURABLE = 4
 
 
 class DensifyParams(ctypes.Structure):
@@ -394,8 +395,11 @@ class Rasterizer:
     records or keys than the current capacity."""
 
     def __init__(self, cams, tile=(16, 16), bg=(0.0, 0.0, 0.0), device="cuda", headroom=1.15, pixels_per_thread=0,
-                 max_bytes=None):
+                 max_bytes=None, capturable=False):
         self.max_bytes = max_bytes  # cap on state + workspace bytes (None: unlimited)
+        # capturable: no count read-backs (CUDA-graph capture); call reserve()
+        # first and check counts() after a step
+        self.capturable = capturable
         self.cams_np = cams
         self.cams_c = make_cameras(cams)
         self.cfg = make_config(tile, bg, pixels_per_thread)
@@ -449,10 +453,11 @@ class Rasterizer:
             self.state = self.workspace = self.layout = None
 
     def _cfg(self, masked=False, depth=False):
-        if not masked and not depth:
+        if not masked and not depth and not self.capturable:
             return self.cfg
         cfg = Config.from_buffer_copy(self.cfg)
-        cfg.flags = (FLAG_MASKED_PARTIAL if masked else 0) | (FLAG_DEPTH if depth else 0)
+        cfg.flags = (FLAG_MASKED_PARTIAL if masked else 0) | (FLAG_DEPTH if depth else 0) | \
+            (FLAG_CAPTURABLE if self.capturable else 0)
         return cfg
 
     def sample_set(self, group: int, seed: int, stream=None) -> SampleSet:
@@ -468,6 +473,19 @@ class Rasterizer:
         n = scene_c.n
         if images is None:
             images = torch.empty(3 * self.pixels, dtype=torch.float32, device=self.device)
+        if self.capturable:
+            # no read-backs, no growing: the caller reserved the capacity and
+            # checks fits() after the step
+            if self.state is None or n != self.n:
+                raise MvgsError(EINVAL, "a capturable rasterizer needs reserve(n, records, keys) first")
+            if samples is None:
+                render_views(scene_c, self.cams_c, self._cfg(False, depth), self.cap, images, self.state,
+                             self.workspace, stream)
+            else:
+                render_views_sampled(scene_c, self.cams_c, self._cfg(masked, depth), self.cap, samples, images,
+                                     self.state, self.workspace, stream)
+            self.needed = Capacity(self.cap.records, self.cap.keys)
+            return images
         self._ensure(n, max(self.cap.records, 1), max(self.cap.keys, 1))
         for _ in range(4):
             try:
@@ -519,4 +537,14 @@ class Rasterizer:
             n_contrib=self._view(L.off_n_contrib, int(L.pixels), torch.int32),
             pixel_stats=self._view(L.off_pixel_stats, int(L.pixels), torch.int32, 2),
             depth_acc=self._view(L.off_pixel_depth, int(L.pixels), torch.float32),
-            counts=self._view(L.off_counts, 4, torch.int64))
+            counts=self._view(L.off_counts, 6, torch.int64))
+
+    def counts(self) -> dict:
+        """The counts block after the last forward (synchronises): records and
+        keys held, and needed (larger after a capturable call ran out of room)."""
+        c = self._view(self.layout.off_counts, 6, torch.int64).cpu().tolist()
+        return dict(records=c[0], keys=c[1], tiles=c[2], pixels=c[3], records_needed=c[4], keys_needed=c[5])
+
+    def fits(self) -> bool:
+        c = self.counts()
+        return c["records_needed"] <= self.cap.records and c["keys_needed"] <= self.cap.keys
