@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph measurements")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrivals per second")
     ap.add_argument("--no-partial", action="store_true",
@@ -216,6 +217,49 @@ def run_ours(args, rank, world):
         ms_batched = float(t.item())
     needed = (int(rz.needed.records), int(rz.needed.keys))
 
+    # ---- the same step captured in a CUDA graph (capturable mode) ----
+    def graphed(rasterizers, tgts, hws, losses, dimgs, wss, rec_caps):
+        """Captures one step over the given rasterizers (one per call) in a
+        CUDA graph; returns (graph, fits) where fits() checks the counts."""
+        bufs = []
+        for rz_, rc in zip(rasterizers, rec_caps):
+            bufs.append((torch.empty(3 * rz_.pixels, device=dev), torch.empty(rc, 2, device=dev),
+                         torch.empty(rc, device=dev)))
+        acc_grads = {k: torch.zeros_like(v) for k, v in params.items()}
+        many = len(rasterizers) > 1
+
+        def gstep():
+            if many:
+                for g_ in acc_grads.values():
+                    g_.zero_()
+            for rz_, t_, h_, l_, d_, w_, (im_, gm_, e_) in zip(rasterizers, tgts, hws, losses, dimgs, wss, bufs):
+                rz_.forward(sc, images=im_)
+                mvgs.dssim_loss(im_, t_, h_, LAMBDA, l_, d_, w_)
+                rz_.backward(sc, d_, grads, gm_, e_)
+                mvgs.adc_accumulate(rz_.state, n, gm_, e_, *acc)
+                if many:
+                    for k in acc_grads:
+                        acc_grads[k].add_(grads[k])
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            gstep()
+        torch.cuda.current_stream().wait_stream(side)
+        graph_ = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph_):
+            gstep()
+        return graph_, (lambda: all(r.fits() for r in rasterizers))
+
+    graph = None
+    if not args.no_graph:
+        rzg = mvgs.Rasterizer(cams, tile=tile, pixels_per_thread=args.ppt, capturable=True, headroom=1.02)
+        rzg.reserve(n, needed[0], needed[1])
+        g_b, fits_b = graphed([rzg], [tgt], [hw], [loss], [dimg], [dssim_ws], [rzg.cap.records])
+        ms_graph, _ = timed(lambda: g_b.replay(), args.steps, args.warmup)
+        graph = {"views_per_s": V * world / (ms_graph / 1e3), "ms_per_step": ms_graph, "counts_fit": fits_b(),
+                 "launches_per_step": None}
+        del g_b
+
     # ---- per-view launch loop: the same library, V = 1, V times ----
     loop = None
     if not args.no_loop:
@@ -242,11 +286,29 @@ def run_ours(args, rank, world):
         ms_loop, _ = timed(loop_step, max(3, args.steps // 2), 2)
         loop = {"views_per_s": V / (ms_loop / 1e3), "ms_per_step": ms_loop,
                 "speedup_batched_over_loop": ms_loop / ms_batched}
+        if not args.no_graph:
+            # the loop captured in one CUDA graph as well (V capturable calls)
+            rzs = []
+            for v, (rv, tv, hv, lv, dv, wv) in enumerate(singles):
+                rg = mvgs.Rasterizer(cams.subset([v]), tile=tile, pixels_per_thread=args.ppt, capturable=True,
+                                     headroom=1.02)
+                rv.forward(sc)
+                rg.reserve(n, int(rv.needed.records), int(rv.needed.keys))
+                rzs.append(rg)
+            g_l, fits_l = graphed(rzs, [x[1] for x in singles], [x[2] for x in singles], [x[3] for x in singles],
+                                  [x[4] for x in singles], [x[5] for x in singles], [r.cap.records for r in rzs])
+            ms_gloop, _ = timed(lambda: g_l.replay(), max(3, args.steps // 2), 2)
+            loop["graphed"] = {"views_per_s": V / (ms_gloop / 1e3), "ms_per_step": ms_gloop,
+                               "counts_fit": fits_l()}
+            if graph:
+                loop["speedup_graphed_batched_over_graphed_loop"] = ms_gloop / graph["ms_per_step"]
+            del g_l, rzs
 
     # ---- partial rendering (Sec. 5.1.1): one image's worth of pixels over the V views ----
     partial = None
     if not args.no_partial:
         ss = rz.sample_set(V, seed=11)
+        ss_strip = rz.sample_set(V, seed=11, cell="strip")
 
         def render_step(samples=None, masked=False):
             rz.forward(sc, samples=samples, masked=masked)
@@ -254,13 +316,15 @@ def run_ours(args, rank, world):
 
         modes = {}
         for name, kw in (("full", {}), ("masked_partial", {"samples": ss, "masked": True}),
-                         ("thread_efficient", {"samples": ss})):
+                         ("thread_efficient", {"samples": ss}),
+                         ("thread_efficient_strip_cells", {"samples": ss_strip})):
             ms_m, st_m = timed(lambda: render_step(**kw), max(3, args.steps // 2), 2, profile=True)
             nst = max(3, args.steps // 2)
             modes[name] = {"render_fwd_bwd_ms": round(ms_m, 4),
                            "blend_forward_ms": round(st_m.get("blend_forward", (0, 0))[0] / nst, 4),
                            "blend_backward_ms": round(st_m.get("blend_backward", (0, 0))[0] / nst, 4)}
         partial = {"group": V, "sampled_pixels": int(ss.offsets[-1].item()), "pixels": rz.pixels,
+                   "sampling": "per pixel (1x1 cells); strip cells: %dx%d" % rz.strip_cell(),
                    "modes": modes,
                    "blend_speedup_thread_efficient_over_masked":
                        (modes["masked_partial"]["blend_forward_ms"] + modes["masked_partial"]["blend_backward_ms"]) /
@@ -305,6 +369,7 @@ def run_ours(args, rank, world):
                                             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "per_view_loop": loop,
+        "cuda_graph": graph,
         "partial_rendering": partial,
         "serving": serving,
         "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in (stages or {}).items() if v[1]},

@@ -218,20 +218,30 @@ typedef struct mvgs_samples {
     const uint16_t* pixels;
 } mvgs_samples;
 
+/* The sampling rule: group, cell size and seed (see mvgs_partial_samples). */
+typedef struct mvgs_sampling {
+    int32_t group;          /* views sharing the pixel positions of a tile */
+    int32_t cell_w, cell_h; /* pixels decided together (1 x 1: pixel by pixel) */
+    uint64_t seed;
+} mvgs_sampling;
+
 /* Scratch bytes for mvgs_partial_samples. */
 size_t mvgs_partial_samples_workspace_size(const mvgs_camera* cams, int32_t V, const mvgs_config* cfg);
 
-/* Fills a sample set: view v renders pixel (x, y) when
+/* Fills a sample set: view v renders pixel (x, y) when its cell
+ * (cx, cy) = (x / cell_w, y / cell_h) has
  *   floor(group * (h >> 32) / 2^32) == v mod group,
- * h = SplitMix64 output number 2^32 y + x + 1 of the stream seeded with
+ * h = SplitMix64 output number 2^32 cy + cx + 1 of the stream seeded with
  * `seed`.  So `group` consecutive views of one resolution split every pixel
  * position between them exactly once (one image's worth of pixels over
  * `group` views), each taking about 1/group of its pixels.  The paper leaves
- * the sub-sampling rule open; this one is seeded and reproducible.
+ * the sub-sampling rule open; this one is seeded and reproducible.  Cells of
+ * tile_w x (32 / tile_w) * pixels_per_thread pixels are exactly the warps'
+ * strips, which keeps every run of samples compact (best culling).
  *   offsets [layout.tiles + 1], pixels [layout.pixels]: device, written.
- * group >= 1; the tile size in cfg must be the one used to render. */
-mvgs_status mvgs_partial_samples(const mvgs_camera* cams, int32_t V, const mvgs_config* cfg, int32_t group,
-                                 uint64_t seed, int64_t* offsets, uint16_t* pixels, void* workspace,
+ * The tile size in cfg must be the one used to render. */
+mvgs_status mvgs_partial_samples(const mvgs_camera* cams, int32_t V, const mvgs_config* cfg,
+                                 const mvgs_sampling* sampling, int64_t* offsets, uint16_t* pixels, void* workspace,
                                  size_t workspace_bytes, mvgs_stream stream);
 
 /* mvgs_render_views restricted to a sample set: writes the images,
@@ -262,8 +272,8 @@ mvgs_status mvgs_render_views_sampled_backward(const mvgs_scene* scene, const mv
  * of `group` consecutive views of one resolution (V a multiple of group);
  * merged image m (packed like the images: [3, H, W] after the previous
  * merged images) takes pixel (x, y) from view m * group + slot(x, y), the
- * view that rendered it under mvgs_partial_samples with the same group and
- * seed. */
+ * view that rendered it under mvgs_partial_samples with the same sampling
+ * rule. */
 
 /* Scratch bytes of mvgs_merge_views / mvgs_split_merged_grad. */
 size_t mvgs_merge_workspace_size(int32_t V);
@@ -279,7 +289,7 @@ size_t mvgs_merge_workspace_size(int32_t V);
  *   sigma  [H, W]     kernel width sigma_px * z / f_x (sigma_px: the 2D
  *                     window's sigma, 1.5), 0 where 1 - final_T < 1e-3 (no
  *                     surface point; such a pixel is only its own neighbour). */
-mvgs_status mvgs_merge_views(const mvgs_camera* cams, int32_t V, int32_t group, uint64_t seed, float sigma_px,
+mvgs_status mvgs_merge_views(const mvgs_camera* cams, int32_t V, const mvgs_sampling* sampling, float sigma_px,
                              const float* images, const float* targets, const float* depth_acc, const float* final_T,
                              float* merged_img, float* merged_tgt, float* points, float* sigma, void* workspace,
                              size_t workspace_bytes, mvgs_stream stream);
@@ -287,7 +297,7 @@ mvgs_status mvgs_merge_views(const mvgs_camera* cams, int32_t V, int32_t group, 
 /* Sends dL/d(merged images) back to the views: each view pixel gets the
  * merged gradient where it is the owner and 0 elsewhere (dL_dimages is
  * fully written, packed per view). */
-mvgs_status mvgs_split_merged_grad(const mvgs_camera* cams, int32_t V, int32_t group, uint64_t seed,
+mvgs_status mvgs_split_merged_grad(const mvgs_camera* cams, int32_t V, const mvgs_sampling* sampling,
                                    const float* dL_dmerged, float* dL_dimages, void* workspace,
                                    size_t workspace_bytes, mvgs_stream stream);
 

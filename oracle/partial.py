@@ -3,11 +3,12 @@
 
 The paper renders, per tile and viewpoint, a sub-sample of the pixels given
 as an index array, and leaves the sampling rule open.  The rule adopted:
-view v renders pixel (x, y) when
+view v renders pixel (x, y) when its cell (cx, cy) = (x // cell_w, y // cell_h)
+has
 
     floor(group * (h >> 32) / 2^32) == v mod group,
 
-h the SplitMix64 output number c + 1, c = 2^32 y + x, of the stream seeded
+h the SplitMix64 output number c + 1, c = 2^32 cy + cx, of the stream seeded
 with `seed` (Steele, Lea & Flood, "Fast splittable pseudorandom number
 generators", OOPSLA 2014): output number k is mix(seed + k * gamma) with
 gamma = 0x9e3779b97f4a7c15 and mix the published 64-bit finalizer.  Written
@@ -48,10 +49,12 @@ def pixel_slot(seed: int, x: int, y: int, group: int) -> int:
     return ((h >> 32) * group) >> 32
 
 
-def slot_image(seed: int, width: int, height: int, group: int) -> np.ndarray:
-    """pixel_slot over a whole image [height, width], vectorised in uint64."""
+def slot_image(seed: int, width: int, height: int, group: int, cell=(1, 1)) -> np.ndarray:
+    """The slot of every pixel of an image [height, width] (its cell's
+    pixel_slot), vectorised in uint64."""
     with np.errstate(over="ignore"):
-        ys, xs = np.meshgrid(np.arange(height, dtype=np.uint64), np.arange(width, dtype=np.uint64), indexing="ij")
+        ys, xs = np.meshgrid(np.arange(height, dtype=np.uint64) // np.uint64(cell[1]),
+                             np.arange(width, dtype=np.uint64) // np.uint64(cell[0]), indexing="ij")
         c = (ys << np.uint64(32)) | xs
         z = np.uint64(seed & MASK64) + (c + np.uint64(1)) * np.uint64(GAMMA)
         z = (z ^ (z >> np.uint64(30))) * np.uint64(M1)
@@ -60,15 +63,15 @@ def slot_image(seed: int, width: int, height: int, group: int) -> np.ndarray:
         return (((h >> np.uint64(32)) * np.uint64(group)) >> np.uint64(32)).astype(np.int64)
 
 
-def sample_masks(cams, group: int, seed: int) -> list[np.ndarray]:
+def sample_masks(cams, group: int, seed: int, cell=(1, 1)) -> list[np.ndarray]:
     """Per view, the boolean [H, W] mask of the pixels it renders."""
     out = []
     for v in range(cams.V):
         W, H = int(cams.width[v]), int(cams.height[v])
-        out.append(slot_image(seed, W, H, group) == (v % group))
+        out.append(slot_image(seed, W, H, group, cell) == (v % group))
     return out
 
 
-def packed_mask(cams, group: int, seed: int) -> np.ndarray:
+def packed_mask(cams, group: int, seed: int, cell=(1, 1)) -> np.ndarray:
     """The sample masks flattened in the packed per-view pixel order."""
-    return np.concatenate([m.reshape(-1) for m in sample_masks(cams, group, seed)])
+    return np.concatenate([m.reshape(-1) for m in sample_masks(cams, group, seed, cell)])

@@ -690,6 +690,10 @@ mvgs_status mvgs_render_views_sampled_backward(const mvgs_scene* scene, const mv
                          g_means, g_log_scales, g_quats, g_opacity_logits, g_sh, g_mean2d, e1, samples, stream);
 }
 
+static bool bad_sampling(const mvgs_sampling* sp) {
+    return !sp || sp->group < 1 || sp->cell_w < 1 || sp->cell_h < 1;
+}
+
 size_t mvgs_partial_samples_workspace_size(const mvgs_camera* cams, int32_t V, const mvgs_config* cfg) {
     Plan P;
     const mvgs_capacity cap{0, 0};
@@ -697,14 +701,14 @@ size_t mvgs_partial_samples_workspace_size(const mvgs_camera* cams, int32_t V, c
     return 256 + ((size_t)V * sizeof(DevCam) + 255) / 256 * 256 + sample_temp_bytes(P.tiles);
 }
 
-mvgs_status mvgs_partial_samples(const mvgs_camera* cams, int32_t V, const mvgs_config* cfg, int32_t group,
-                                 uint64_t seed, int64_t* offsets, uint16_t* pixels, void* workspace,
+mvgs_status mvgs_partial_samples(const mvgs_camera* cams, int32_t V, const mvgs_config* cfg,
+                                 const mvgs_sampling* sampling, int64_t* offsets, uint16_t* pixels, void* workspace,
                                  size_t workspace_bytes, mvgs_stream stream) {
     Plan P;
     const mvgs_capacity cap{0, 0};
     mvgs_status st = make_plan(0, cams, V, cfg, &cap, P);
     if (st != MVGS_OK) return st;
-    if (group < 1) return fail(MVGS_EINVAL, "group must be >= 1");
+    if (bad_sampling(sampling)) return fail(MVGS_EINVAL, "sampling: group and cell sides must be >= 1");
     if (!offsets || !pixels || !workspace) return fail(MVGS_EINVAL, "NULL offsets, pixels or workspace");
     const size_t cam_bytes = ((size_t)V * sizeof(DevCam) + 255) / 256 * 256;
     const size_t need = 256 + cam_bytes + sample_temp_bytes(P.tiles);
@@ -714,8 +718,9 @@ mvgs_status mvgs_partial_samples(const mvgs_camera* cams, int32_t V, const mvgs_
     char* base = reinterpret_cast<char*>(((uintptr_t)workspace + 255) / 256 * 256);
     DevCam* dcams = reinterpret_cast<DevCam*>(base);
     upload_cams(P.cams.data(), V, dcams, s);
-    launch_partial_samples(dcams, V, P.tiles, cfg->tile_w, cfg->tile_h, group, (unsigned long long)seed,
-                           reinterpret_cast<long long*>(offsets), pixels, base + cam_bytes, s);
+    launch_partial_samples(dcams, V, P.tiles, cfg->tile_w, cfg->tile_h, sampling->group, sampling->cell_w,
+                           sampling->cell_h, (unsigned long long)sampling->seed, reinterpret_cast<long long*>(offsets),
+                           pixels, base + cam_bytes, s);
     return cuda_check("partial samples");
 }
 
@@ -756,10 +761,12 @@ static mvgs_status merge_upload(const Plan& P, const std::vector<long long>& mb,
     return MVGS_OK;
 }
 
-mvgs_status mvgs_merge_views(const mvgs_camera* cams, int32_t V, int32_t group, uint64_t seed, float sigma_px,
+mvgs_status mvgs_merge_views(const mvgs_camera* cams, int32_t V, const mvgs_sampling* sampling, float sigma_px,
                              const float* images, const float* targets, const float* depth_acc, const float* final_T,
                              float* merged_img, float* merged_tgt, float* points, float* sigma, void* workspace,
                              size_t workspace_bytes, mvgs_stream stream) {
+    if (bad_sampling(sampling)) return fail(MVGS_EINVAL, "sampling: group and cell sides must be >= 1");
+    const int group = sampling->group;
     Plan P;
     std::vector<long long> mb;
     mvgs_status st = merge_plan(cams, V, group, P, mb);
@@ -772,14 +779,17 @@ mvgs_status mvgs_merge_views(const mvgs_camera* cams, int32_t V, int32_t group, 
     DevCam* dcams;
     long long* dmb;
     if ((st = merge_upload(P, mb, workspace, workspace_bytes, s, &dcams, &dmb)) != MVGS_OK) return st;
-    launch_merge_views(dcams, group, (unsigned long long)seed, sigma_px, mb.back(), dmb, V / group, images, targets,
-                       depth_acc, final_T, merged_img, merged_tgt, points, sigma, s);
+    launch_merge_views(dcams, group, sampling->cell_w, sampling->cell_h, (unsigned long long)sampling->seed, sigma_px,
+                       mb.back(), dmb, V / group, images, targets, depth_acc, final_T, merged_img, merged_tgt, points,
+                       sigma, s);
     return cuda_check("merge views");
 }
 
-mvgs_status mvgs_split_merged_grad(const mvgs_camera* cams, int32_t V, int32_t group, uint64_t seed,
+mvgs_status mvgs_split_merged_grad(const mvgs_camera* cams, int32_t V, const mvgs_sampling* sampling,
                                    const float* dL_dmerged, float* dL_dimages, void* workspace,
                                    size_t workspace_bytes, mvgs_stream stream) {
+    if (bad_sampling(sampling)) return fail(MVGS_EINVAL, "sampling: group and cell sides must be >= 1");
+    const int group = sampling->group;
     Plan P;
     std::vector<long long> mb;
     mvgs_status st = merge_plan(cams, V, group, P, mb);
@@ -789,7 +799,8 @@ mvgs_status mvgs_split_merged_grad(const mvgs_camera* cams, int32_t V, int32_t g
     DevCam* dcams;
     long long* dmb;
     if ((st = merge_upload(P, mb, workspace, workspace_bytes, s, &dcams, &dmb)) != MVGS_OK) return st;
-    launch_split_merged(dcams, group, (unsigned long long)seed, mb.back(), dmb, V / group, dL_dmerged, dL_dimages, s);
+    launch_split_merged(dcams, group, sampling->cell_w, sampling->cell_h, (unsigned long long)sampling->seed, mb.back(),
+                        dmb, V / group, dL_dmerged, dL_dimages, s);
     return cuda_check("split merged gradient");
 }
 

@@ -71,8 +71,9 @@ __device__ __forceinline__ int find_view(const DevCam* cams, int V, long long gt
 
 // SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output number k of the
 // stream seeded with s is mix(s + k * 0x9e3779b97f4a7c15).  The partial-render
-// sample slot of pixel (x, y) in a group of `group` views is
-// floor(group * (h >> 32) / 2^32) with h output number 2^32 y + x + 1.
+// sample slot of cell (x, y) in a group of `group` views is
+// floor(group * (h >> 32) / 2^32) with h output number 2^32 y + x + 1; a
+// pixel's cell is (px / cell_w, py / cell_h).
 __device__ __forceinline__ unsigned long long splitmix64_mix(unsigned long long z) {
     z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
     z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;

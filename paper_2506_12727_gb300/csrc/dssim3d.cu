@@ -254,7 +254,8 @@ __global__ void dssim3d_reduce_kernel(Images im, const float2* __restrict__ bsum
 }
 
 // ---- merge / split ---------------------------------------------------------
-__global__ void merge_kernel(const DevCam* __restrict__ cams, int group, unsigned long long seed, float sigma_px,
+__global__ void merge_kernel(const DevCam* __restrict__ cams, int group, int cw, int ch, unsigned long long seed,
+                             float sigma_px,
                              long long merged_pix, const long long* __restrict__ mbase, int M,
                              const float* __restrict__ images, const float* __restrict__ targets,
                              const float* __restrict__ depth_acc, const float* __restrict__ final_T,
@@ -267,7 +268,7 @@ __global__ void merge_kernel(const DevCam* __restrict__ cams, int group, unsigne
     const DevCam& c0 = cams[m * group];
     const long long local = gp - mbase[m];
     const int x = (int)(local % c0.W), y = (int)(local / c0.W);
-    const int v = m * group + sample_slot(seed, x, y, group);
+    const int v = m * group + sample_slot(seed, x / cw, y / ch, group);
     const DevCam& cam = cams[v];
     const long long HW = (long long)cam.W * cam.H;
     const long long src = (long long)y * cam.W + x;
@@ -290,7 +291,7 @@ __global__ void merge_kernel(const DevCam* __restrict__ cams, int group, unsigne
     out_sig[gp] = s;
 }
 
-__global__ void split_kernel(const DevCam* __restrict__ cams, int group, unsigned long long seed,
+__global__ void split_kernel(const DevCam* __restrict__ cams, int group, int cw, int ch, unsigned long long seed,
                              long long merged_pix, const long long* __restrict__ mbase, int M,
                              const float* __restrict__ dmerged, float* __restrict__ dimg) {
     const long long gp = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -300,7 +301,7 @@ __global__ void split_kernel(const DevCam* __restrict__ cams, int group, unsigne
     const DevCam& c0 = cams[m * group];
     const long long local = gp - mbase[m];
     const int x = (int)(local % c0.W), y = (int)(local / c0.W);
-    const int owner = sample_slot(seed, x, y, group);
+    const int owner = sample_slot(seed, x / cw, y / ch, group);
     const long long HW = (long long)c0.W * c0.H;
     for (int k = 0; k < group; k++) {
         const DevCam& cam = cams[m * group + k];
@@ -370,21 +371,22 @@ void launch_dssim3d(const float* img, const float* target, const float* points, 
     }
 }
 
-void launch_merge_views(const DevCam* cams, int group, unsigned long long seed, float sigma_px, long long merged_pix,
+void launch_merge_views(const DevCam* cams, int group, int cw, int ch, unsigned long long seed, float sigma_px,
+                        long long merged_pix,
                         const long long* mbase, int M, const float* images, const float* targets,
                         const float* depth_acc, const float* final_T, float* out_img, float* out_tgt, float* out_pts,
                         float* out_sig, cudaStream_t s) {
     if (merged_pix <= 0) return;
-    merge_kernel<<<(unsigned)((merged_pix + 255) / 256), 256, 0, s>>>(cams, group, seed, sigma_px, merged_pix, mbase,
-                                                                       M, images, targets, depth_acc, final_T, out_img,
-                                                                       out_tgt, out_pts, out_sig);
+    merge_kernel<<<(unsigned)((merged_pix + 255) / 256), 256, 0, s>>>(cams, group, cw, ch, seed, sigma_px, merged_pix,
+                                                                       mbase, M, images, targets, depth_acc, final_T,
+                                                                       out_img, out_tgt, out_pts, out_sig);
     note_launches(1);
 }
 
-void launch_split_merged(const DevCam* cams, int group, unsigned long long seed, long long merged_pix,
+void launch_split_merged(const DevCam* cams, int group, int cw, int ch, unsigned long long seed, long long merged_pix,
                          const long long* mbase, int M, const float* dmerged, float* dimg, cudaStream_t s) {
     if (merged_pix <= 0) return;
-    split_kernel<<<(unsigned)((merged_pix + 255) / 256), 256, 0, s>>>(cams, group, seed, merged_pix, mbase, M,
+    split_kernel<<<(unsigned)((merged_pix + 255) / 256), 256, 0, s>>>(cams, group, cw, ch, seed, merged_pix, mbase, M,
                                                                        dmerged, dimg);
     note_launches(1);
 }

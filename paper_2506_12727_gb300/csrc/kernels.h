@@ -142,7 +142,7 @@ void launch_blend_backward(const BlendArgs& a, int* counter, const float* dimg, 
 // Pixel selection of the partial render: view v takes pixel (x, y) when the
 // SplitMix64 hash of (seed, x, y) falls in slot v mod `group` of `group`.
 size_t sample_temp_bytes(long long tiles);
-void launch_partial_samples(const DevCam* cams, int V, long long tiles, int tw, int th, int group,
+void launch_partial_samples(const DevCam* cams, int V, long long tiles, int tw, int th, int group, int cw, int ch,
                             unsigned long long seed, long long* s_off, uint16_t* s_pix, void* tmp, cudaStream_t s);
 // Runs of 32 * ppt samples per tile in the blend's tile order.
 size_t chunk_temp_bytes(long long tiles);
@@ -157,11 +157,12 @@ size_t dssim3d_temp_bytes(const int* hw, int M);
 void launch_dssim3d(const float* img, const float* target, const float* points, const float* sigma, const int* hw,
                     int M, float lambda, float* loss, float* dimg, void* tmp, cudaStream_t s);
 // mbase: device [M + 1] first pixel of each merged image; cams: device, all V views
-void launch_merge_views(const DevCam* cams, int group, unsigned long long seed, float sigma_px, long long merged_pix,
+void launch_merge_views(const DevCam* cams, int group, int cw, int ch, unsigned long long seed, float sigma_px,
+                        long long merged_pix,
                         const long long* mbase, int M, const float* images, const float* targets,
                         const float* depth_acc, const float* final_T, float* out_img, float* out_tgt, float* out_pts,
                         float* out_sig, cudaStream_t s);
-void launch_split_merged(const DevCam* cams, int group, unsigned long long seed, long long merged_pix,
+void launch_split_merged(const DevCam* cams, int group, int cw, int ch, unsigned long long seed, long long merged_pix,
                          const long long* mbase, int M, const float* dmerged, float* dimg, cudaStream_t s);
 
 // ---- train.cu ---------------------------------------------------------------

@@ -2,10 +2,13 @@
 //
 // The paper sub-samples, for every tile, the pixels each viewpoint renders and
 // hands the rasterizer an index array per (tile, viewpoint).  The selection
-// rule is not given; here view v renders pixel (x, y) when
-//     slot(x, y) = floor(group * (h(x, y) >> 32) / 2^32) == v mod group,
-//     h(x, y) = SplitMix64 output number (2^32 y + x + 1) of the stream seeded
-//               with `seed` (Steele, Lea & Flood, OOPSLA 2014),
+// rule is not given; here view v renders pixel (x, y) when its cell
+// (cx, cy) = (x / cell_w, y / cell_h) has
+//     slot(cx, cy) = floor(group * (h >> 32) / 2^32) == v mod group,
+//     h = SplitMix64 output number (2^32 cy + cx + 1) of the stream seeded
+//         with `seed` (Steele, Lea & Flood, OOPSLA 2014)
+// (1 x 1 cells: pixel by pixel; cells of a warp's strip keep the samples of a
+// run together),
 // so views v, v + group, ... take the same pixels and, for views of one
 // resolution, any `group` consecutive views split every pixel position
 // between them exactly once (the merged image of Fig. 3c).  Each tile's
@@ -16,8 +19,8 @@
 namespace mvgs {
 namespace {
 
-__device__ __forceinline__ bool sampled(unsigned long long seed, int x, int y, int group, int v) {
-    return sample_slot(seed, x, y, group) == v % group;
+__device__ __forceinline__ bool sampled(unsigned long long seed, int x, int y, int group, int cw, int ch, int v) {
+    return sample_slot(seed, x / cw, y / ch, group) == v % group;
 }
 
 struct TileGeom {
@@ -37,14 +40,14 @@ __device__ __forceinline__ TileGeom tile_geom(const DevCam* cams, int V, long lo
 }
 
 // One block per tile: number of samples.
-__global__ void sample_count_kernel(const DevCam* __restrict__ cams, int V, int tw, int th, int group,
+__global__ void sample_count_kernel(const DevCam* __restrict__ cams, int V, int tw, int th, int group, int cw, int ch,
                                     unsigned long long seed, int* __restrict__ counts) {
     const long long gt = blockIdx.x;
     const TileGeom g = tile_geom(cams, V, gt, tw, th);
     int n = 0;
     for (int i = threadIdx.x; i < tw * th; i += blockDim.x) {
         const int lx = i % tw, ly = i / tw;
-        if (lx < g.w && ly < g.h && sampled(seed, g.x0 + lx, g.y0 + ly, group, g.v)) n++;
+        if (lx < g.w && ly < g.h && sampled(seed, g.x0 + lx, g.y0 + ly, group, cw, ch, g.v)) n++;
     }
     __shared__ int warp_n[32];
     for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
@@ -58,7 +61,7 @@ __global__ void sample_count_kernel(const DevCam* __restrict__ cams, int V, int 
 }
 
 // One block per tile: the samples in raster order.
-__global__ void sample_fill_kernel(const DevCam* __restrict__ cams, int V, int tw, int th, int group,
+__global__ void sample_fill_kernel(const DevCam* __restrict__ cams, int V, int tw, int th, int group, int cw, int ch,
                                    unsigned long long seed, const long long* __restrict__ s_off,
                                    uint16_t* __restrict__ s_pix) {
     const long long gt = blockIdx.x;
@@ -72,7 +75,8 @@ __global__ void sample_fill_kernel(const DevCam* __restrict__ cams, int V, int t
     for (int i0 = 0; i0 < tw * th; i0 += blockDim.x) {
         const int i = i0 + threadIdx.x;
         const int lx = i % tw, ly = i / tw;
-        const bool take = i < tw * th && lx < g.w && ly < g.h && sampled(seed, g.x0 + lx, g.y0 + ly, group, g.v);
+        const bool take =
+            i < tw * th && lx < g.w && ly < g.h && sampled(seed, g.x0 + lx, g.y0 + ly, group, cw, ch, g.v);
         const unsigned bal = __ballot_sync(0xffffffffu, take);
         if (lane == 0) warp_n[w] = __popc(bal);
         __syncthreads();
@@ -133,14 +137,14 @@ size_t sample_temp_bytes(long long tiles) {
     return ((size_t)(tiles > 0 ? tiles : 1) * sizeof(int) + 255) / 256 * 256 + scan_temp_bytes((uint64_t)tiles);
 }
 
-void launch_partial_samples(const DevCam* cams, int V, long long tiles, int tw, int th, int group,
+void launch_partial_samples(const DevCam* cams, int V, long long tiles, int tw, int th, int group, int cw, int ch,
                             unsigned long long seed, long long* s_off, uint16_t* s_pix, void* tmp, cudaStream_t s) {
     if (tiles <= 0) return;
     int* counts = static_cast<int*>(tmp);
     void* scan_tmp = static_cast<char*>(tmp) + ((size_t)tiles * sizeof(int) + 255) / 256 * 256;
-    sample_count_kernel<<<(unsigned)tiles, 256, 0, s>>>(cams, V, tw, th, group, seed, counts);
+    sample_count_kernel<<<(unsigned)tiles, 256, 0, s>>>(cams, V, tw, th, group, cw, ch, seed, counts);
     scan_i32_to_i64(counts, s_off, (uint64_t)tiles, scan_tmp, s);
-    sample_fill_kernel<<<(unsigned)tiles, 256, 0, s>>>(cams, V, tw, th, group, seed, s_off, s_pix);
+    sample_fill_kernel<<<(unsigned)tiles, 256, 0, s>>>(cams, V, tw, th, group, cw, ch, seed, s_off, s_pix);
     note_launches(2);
 }
 

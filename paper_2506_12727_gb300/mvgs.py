@@ -55,6 +55,11 @@ class Samples(ctypes.Structure):
     _fields_ = [("offsets", ctypes.c_void_p), ("pixels", ctypes.c_void_p)]
 
 
+class Sampling(ctypes.Structure):
+    _fields_ = [("group", ctypes.c_int32), ("cell_w", ctypes.c_int32), ("cell_h", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
 FLAG_MASKED_PARTIAL = 1
 FLAG_DEPTH = 2
 FLAG_CAPTURABLE = 4
@@ -105,11 +110,11 @@ def load_library(path: str | None = None):
                                                        P]
     lib.mvgs_partial_samples_workspace_size.argtypes = [P, I32, P]
     lib.mvgs_partial_samples_workspace_size.restype = SZ
-    lib.mvgs_partial_samples.argtypes = [P, I32, P, I32, ctypes.c_uint64, P, P, P, SZ, P]
+    lib.mvgs_partial_samples.argtypes = [P, I32, P, P, P, P, P, SZ, P]
     lib.mvgs_merge_workspace_size.argtypes = [I32]
     lib.mvgs_merge_workspace_size.restype = SZ
-    lib.mvgs_merge_views.argtypes = [P, I32, I32, ctypes.c_uint64, ctypes.c_float, P, P, P, P, P, P, P, P, P, SZ, P]
-    lib.mvgs_split_merged_grad.argtypes = [P, I32, I32, ctypes.c_uint64, P, P, P, SZ, P]
+    lib.mvgs_merge_views.argtypes = [P, I32, P, ctypes.c_float, P, P, P, P, P, P, P, P, P, SZ, P]
+    lib.mvgs_split_merged_grad.argtypes = [P, I32, P, P, P, P, SZ, P]
     lib.mvgs_dssim3d_workspace_size.argtypes = [P, I32]
     lib.mvgs_dssim3d_workspace_size.restype = SZ
     lib.mvgs_dssim3d_loss.argtypes = [P, P, P, P, P, I32, ctypes.c_float, P, P, P, SZ, P]
@@ -246,15 +251,20 @@ class SampleSet:
         return self.pixels[:n].to(torch.int64) & 0xFFFF
 
 
-def partial_samples(cams_c, cfg, group: int, seed: int, device="cuda", stream=None) -> SampleSet:
-    """mvgs_partial_samples: view v takes the pixels whose hash slot is v mod group."""
+def sampling(group: int, seed: int, cell=(1, 1)) -> Sampling:
+    return Sampling(int(group), int(cell[0]), int(cell[1]), int(seed))
+
+
+def partial_samples(cams_c, cfg, group: int, seed: int, device="cuda", stream=None, cell=(1, 1)) -> SampleSet:
+    """mvgs_partial_samples: view v takes the cells whose hash slot is v mod group."""
     L = render_layout(0, cams_c, cfg, Capacity(0, 0))
     offsets = torch.empty(int(L.tiles) + 1, dtype=torch.int64, device=device)
     pixels = torch.empty(max(int(L.pixels), 1), dtype=torch.int16, device=device)
     nbytes = int(_lib.mvgs_partial_samples_workspace_size(cams_c, len(cams_c), ctypes.byref(cfg)))
     ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device)
-    _check(_lib.mvgs_partial_samples(cams_c, len(cams_c), ctypes.byref(cfg), int(group), ctypes.c_uint64(seed),
-                                     _ptr(offsets), _ptr(pixels), _ptr(ws), ws.numel(), _stream(stream)))
+    sp = sampling(group, seed, cell)
+    _check(_lib.mvgs_partial_samples(cams_c, len(cams_c), ctypes.byref(cfg), ctypes.byref(sp), _ptr(offsets),
+                                     _ptr(pixels), _ptr(ws), ws.numel(), _stream(stream)))
     return SampleSet(offsets, pixels)
 
 
@@ -280,17 +290,19 @@ def render_views_sampled_backward(scene_c, cams_c, cfg, cap, samples: SampleSet,
 
 
 def merge_views(cams_c, group, seed, images=None, targets=None, depth_acc=None, final_T=None, merged_img=None,
-                merged_tgt=None, points=None, sigma=None, sigma_px=1.5, stream=None):
+                merged_tgt=None, points=None, sigma=None, sigma_px=1.5, stream=None, cell=(1, 1)):
     """mvgs_merge_views (outputs are caller tensors; None skips)."""
     ws = torch.empty(int(_lib.mvgs_merge_workspace_size(len(cams_c))), dtype=torch.uint8, device="cuda")
-    _check(_lib.mvgs_merge_views(cams_c, len(cams_c), int(group), ctypes.c_uint64(seed), ctypes.c_float(sigma_px),
+    sp = sampling(group, seed, cell)
+    _check(_lib.mvgs_merge_views(cams_c, len(cams_c), ctypes.byref(sp), ctypes.c_float(sigma_px),
                                  _ptr(images), _ptr(targets), _ptr(depth_acc), _ptr(final_T), _ptr(merged_img),
                                  _ptr(merged_tgt), _ptr(points), _ptr(sigma), _ptr(ws), ws.numel(), _stream(stream)))
 
 
-def split_merged_grad(cams_c, group, seed, dL_dmerged, dL_dimages, stream=None):
+def split_merged_grad(cams_c, group, seed, dL_dmerged, dL_dimages, stream=None, cell=(1, 1)):
     ws = torch.empty(int(_lib.mvgs_merge_workspace_size(len(cams_c))), dtype=torch.uint8, device="cuda")
-    _check(_lib.mvgs_split_merged_grad(cams_c, len(cams_c), int(group), ctypes.c_uint64(seed), _ptr(dL_dmerged),
+    sp = sampling(group, seed, cell)
+    _check(_lib.mvgs_split_merged_grad(cams_c, len(cams_c), ctypes.byref(sp), _ptr(dL_dmerged),
                                        _ptr(dL_dimages), _ptr(ws), ws.numel(), _stream(stream)))
 
 
@@ -460,9 +472,20 @@ class Rasterizer:
             (FLAG_CAPTURABLE if self.capturable else 0)
         return cfg
 
-    def sample_set(self, group: int, seed: int, stream=None) -> SampleSet:
-        """Seeded partial-render samples for these cameras and this tile size."""
-        return partial_samples(self.cams_c, self.cfg, group, seed, self.device, stream)
+    def sample_set(self, group: int, seed: int, stream=None, cell=(1, 1)) -> SampleSet:
+        """Seeded partial-render samples for these cameras and this tile size
+        (cell="strip": cells of one warp's strip)."""
+        if cell == "strip":
+            cell = self.strip_cell()
+        return partial_samples(self.cams_c, self.cfg, group, seed, self.device, stream, cell)
+
+    def strip_cell(self):
+        """(tile_w, rows of a warp's strip) for this tile size and pixels per lane."""
+        tw, th = self.cfg.tile_w, self.cfg.tile_h
+        ppt = self.cfg.pixels_per_thread
+        if ppt == 0:
+            ppt = next(p for p in (4, 2, 1) if th % ((32 // tw) * p) == 0)
+        return (tw, (32 // tw) * ppt)
 
     def forward(self, scene_c, images=None, stream=None, samples: SampleSet | None = None, masked=False,
                 depth=False):

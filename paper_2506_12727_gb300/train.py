@@ -37,7 +37,7 @@ DEFAULT_LR = dict(means=1.6e-4, log_scales=5e-3, quats=1e-3, opacity_logits=5e-2
 class MultiViewTrainer:
     def __init__(self, params: dict, sh_degree: int, cams, targets, views_per_iter=4, tile=(16, 16),
                  partial=False, lam=0.2, lr=None, densify_every=0, split_threshold=2e-4, clone_threshold=2e-4,
-                 prune_opacity=0.005, dense_extent=0.01, seed=0, device="cuda"):
+                 prune_opacity=0.005, dense_extent=0.01, seed=0, device="cuda", cell=(1, 1)):
         """`cams`: all training cameras (numpy camera set); `targets`: list of
         [3, H, W] device tensors, one per camera.  Thresholds are in the units
         of the statistics (pixel-space gradient norms, averaged over views)."""
@@ -48,6 +48,7 @@ class MultiViewTrainer:
         self.V = views_per_iter
         self.tile = tuple(tile)
         self.partial = partial
+        self.cell = cell  # partial sampling cell: (1, 1) pixel by pixel, "strip" one warp strip
         self.lam = lam
         self.lr = dict(DEFAULT_LR, **(lr or {}))
         self.densify_every = densify_every
@@ -98,7 +99,8 @@ class MultiViewTrainer:
         else:
             if not (cams.width == cams.width[0]).all() or not (cams.height == cams.height[0]).all():
                 raise ValueError("partial rendering merges views of one resolution")
-            samples = rz.sample_set(cams.V, seed=int(self.t))
+            samples = rz.sample_set(cams.V, seed=int(self.t), cell=self.cell)
+            cell = rz.strip_cell() if self.cell == "strip" else self.cell
             img = torch.zeros(3 * rz.pixels, device=self.device)
             rz.forward(sc, images=img, samples=samples, depth=True)
             rec = rz.records()
@@ -108,14 +110,14 @@ class MultiViewTrainer:
             pts = torch.empty_like(mimg)
             sig = torch.empty(H * W, device=self.device)
             mvgs.merge_views(rz.cams_c, cams.V, int(self.t), img, tgt, rec["depth_acc"], rec["final_T"], mimg, mtgt,
-                             pts, sig)
+                             pts, sig, cell=cell)
             mhw = np.array([[H, W]], np.int32)
             loss = torch.empty(1, device=self.device)
             dm = torch.empty_like(mimg)
             ws = torch.empty(mvgs.dssim3d_workspace_size(mhw), dtype=torch.uint8, device=self.device)
             mvgs.dssim3d_loss(mimg, mtgt, pts, sig, mhw, self.lam, loss, dm, ws)
             dimg = torch.empty_like(img)
-            mvgs.split_merged_grad(rz.cams_c, cams.V, int(self.t), dm, dimg)
+            mvgs.split_merged_grad(rz.cams_c, cams.V, int(self.t), dm, dimg, cell=cell)
         R = int(rz.needed.records)
         gm2d = torch.empty(max(R, 1), 2, device=self.device)
         e1 = torch.empty(max(R, 1), device=self.device)

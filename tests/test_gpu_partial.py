@@ -66,14 +66,15 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("cell", [(1, 1), (16, 8), (3, 5)])
 @pytest.mark.parametrize("group", [1, 2, 3, 4, 8])
 @pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 16), (16, 64)])
-def test_samples_match_oracle_selection(cuda_lib, tile, group):
+def test_samples_match_oracle_selection(cuda_lib, tile, group, cell):
     _, cams = CASES["ragged_3views"]
     rz = cuda_lib.Rasterizer(cams, tile=tile)
-    ss = rz.sample_set(group, seed=1234)
+    ss = rz.sample_set(group, seed=1234, cell=cell)
     got = _masks_from_samples(ss, cams, tile)
-    np.testing.assert_array_equal(got, partial.packed_mask(cams, group, 1234))
+    np.testing.assert_array_equal(got, partial.packed_mask(cams, group, 1234, cell))
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
@@ -87,8 +88,8 @@ def test_sampled_pixels_equal_full_render(cuda_lib, case, tile, ppt):
     full = rz.forward(sc).clone()
     fT = rz.records()["final_T"].clone()
     fN = rz.records()["n_contrib"].clone()
-    for group in (2, 3):
-        ss = rz.sample_set(group, seed=77 + group)
+    for group, cell in ((2, (1, 1)), (3, (1, 1)), (4, "strip")):
+        ss = rz.sample_set(group, seed=77 + group, cell=cell)
         m = _masks_from_samples(ss, cams, tile)
         m3 = torch.tensor(_packed3(m, cams), device="cuda")
         mt = torch.tensor(m, device="cuda")

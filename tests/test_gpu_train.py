@@ -84,8 +84,8 @@ def test_adam_matches_torch(cuda_lib):
     np.testing.assert_allclose(p.cpu().numpy(), ref.detach().numpy(), rtol=0, atol=2e-6)
 
 
-@pytest.mark.parametrize("partial", [False, True])
-def test_training_loop_reduces_the_loss(cuda_lib, partial):
+@pytest.mark.parametrize("partial,cell", [(False, (1, 1)), (True, (1, 1)), (True, "strip")])
+def test_training_loop_reduces_the_loss(cuda_lib, partial, cell):
     import synth
     from gpu_helpers import scene_to_device
     from paper_2506_12727_gb300.train import MultiViewTrainer
@@ -100,7 +100,7 @@ def test_training_loop_reduces_the_loss(cuda_lib, partial):
     init["means"] += torch.tensor(rng.normal(0, 0.02, size=(3000, 3)), dtype=torch.float32, device="cuda")
     init["sh"][:, 0] += torch.tensor(rng.normal(0, 0.3, size=(3000, 3)), dtype=torch.float32, device="cuda")
     init["opacity_logits"] -= 1.0
-    tr = MultiViewTrainer(init, 1, cams, targets, views_per_iter=4, partial=partial, densify_every=30,
+    tr = MultiViewTrainer(init, 1, cams, targets, views_per_iter=4, partial=partial, densify_every=30, cell=cell,
                           lr=dict(means=1e-3, sh=1e-2), clone_threshold=1e-3, split_threshold=1e-3,
                           prune_opacity=0.004, dense_extent=0.06, seed=1)
     losses = [tr.step() for _ in range(60)]

@@ -22,6 +22,14 @@ def test_vectorised_slots_match_scalar_definition():
             assert img.min() >= 0 and img.max() < group
 
 
+def test_cells_share_one_slot():
+    img = partial.slot_image(7, 40, 30, 4, cell=(16, 8))
+    for cy in range(0, 30, 8):
+        for cx in range(0, 40, 16):
+            blk = img[cy:cy + 8, cx:cx + 16]
+            assert (blk == partial.pixel_slot(7, cx // 16, cy // 8, 4)).all()
+
+
 def test_views_of_a_group_partition_the_pixels():
     cams = synth.make_cameras([(64, 48)] * 4, seed=1)
     for group in (1, 2, 4):
