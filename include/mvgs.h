@@ -171,6 +171,15 @@ typedef struct mvgs_layout {
 mvgs_status mvgs_render_layout(int64_t n, const mvgs_camera* cams, int32_t V, const mvgs_config* cfg,
                                const mvgs_capacity* cap, mvgs_layout* out);
 
+/* Participation pre-count (the supplement's test of which Gaussians take part
+ * in which view, done before anything is allocated): the exact record and key
+ * counts mvgs_render_views will need for this scene, cameras and tile size,
+ * without writing records.  For admission and for sizing buffers (e.g. a
+ * capturable rasterizer) ahead of a batch.  Synchronises `stream`. */
+size_t mvgs_count_workspace_size(int64_t n, int32_t V);
+mvgs_status mvgs_count_views(const mvgs_scene* scene, const mvgs_camera* cams, int32_t V, const mvgs_config* cfg,
+                             mvgs_capacity* needed, void* workspace, size_t workspace_bytes, mvgs_stream stream);
+
 /* Forward render of V views (Eq. 1; preprocessing of the supplement).
  *   images     [3 * pixels] float32 out, packed per view (see top).
  *   state      >= layout.state_bytes, written; keep it for the backward.

@@ -690,6 +690,57 @@ mvgs_status mvgs_render_views_sampled_backward(const mvgs_scene* scene, const mv
                          g_means, g_log_scales, g_quats, g_opacity_logits, g_sh, g_mean2d, e1, samples, stream);
 }
 
+// ---- participation pre-count -------------------------------------------------
+static size_t count_ws_parts(long long n, size_t* a, size_t* b, size_t* c) {
+    const long long nn = n > 0 ? n : 1;
+    *a = ((size_t)nn * sizeof(int) + 255) / 256 * 256;
+    *b = ((size_t)(nn + 1) * sizeof(long long) + 255) / 256 * 256;
+    *c = scan_temp_bytes((uint64_t)nn);
+    return 256 + 2 * *a + 2 * *b + *c;
+}
+
+size_t mvgs_count_workspace_size(int64_t n, int32_t V) {
+    size_t a, b, c;
+    return count_ws_parts(n, &a, &b, &c) + ((size_t)(V > 0 ? V : 1) * sizeof(DevCam) + 255) / 256 * 256;
+}
+
+mvgs_status mvgs_count_views(const mvgs_scene* scene, const mvgs_camera* cams, int32_t V, const mvgs_config* cfg,
+                             mvgs_capacity* needed, void* workspace, size_t workspace_bytes, mvgs_stream stream) {
+    mvgs_status st = check_scene(scene);
+    if (st != MVGS_OK) return st;
+    Plan P;
+    const mvgs_capacity cap{0, 0};
+    if ((st = make_plan(scene->n, cams, V, cfg, &cap, P)) != MVGS_OK) return st;
+    if (!needed || !workspace) return fail(MVGS_EINVAL, "NULL needed or workspace");
+    if (workspace_bytes < mvgs_count_workspace_size(scene->n, V))
+        return fail(MVGS_ENOSPACE, "workspace %zu < %zu bytes", workspace_bytes,
+                    mvgs_count_workspace_size(scene->n, V));
+    size_t a, b, c;
+    count_ws_parts(scene->n, &a, &b, &c);
+    char* base = reinterpret_cast<char*>(((uintptr_t)workspace + 255) / 256 * 256);
+    int* recs = reinterpret_cast<int*>(base);
+    uint32_t* keys = reinterpret_cast<uint32_t*>(base + a);
+    long long* roff = reinterpret_cast<long long*>(base + 2 * a);
+    unsigned long long* koff = reinterpret_cast<unsigned long long*>(base + 2 * a + b);
+    void* scan_tmp = base + 2 * a + 2 * b;
+    DevCam* dcams = reinterpret_cast<DevCam*>(base + 2 * a + 2 * b + c);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    upload_cams(P.cams.data(), V, dcams, s);
+    const long long n = scene->n;
+    launch_count_keys(scene_args(scene), dcams, V, cfg->tile_w, cfg->tile_h, recs, keys, s);
+    scan_i32_to_i64(recs, roff, (uint64_t)n, scan_tmp, s);
+    scan_u32_to_u64(keys, koff, (uint64_t)n, scan_tmp, s);
+    long long R = 0;
+    unsigned long long K = 0;
+    if (cudaMemcpyAsync(&R, roff + n, sizeof(R), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&K, koff + n, sizeof(K), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return cuda_check("count read-back");
+    needed->records = R;
+    needed->keys = (long long)K;
+    return cuda_check("count views");
+}
+
 static bool bad_sampling(const mvgs_sampling* sp) {
     return !sp || sp->group < 1 || sp->cell_w < 1 || sp->cell_h < 1;
 }

@@ -42,6 +42,9 @@ struct RecordArgs {
     long long cap;       // records the arrays hold: no record index reaches it
 };
 
+// Per Gaussian: visible views and covered tiles (sizing only; no records).
+void launch_count_keys(const SceneArgs& sc, const DevCam* cams, int V, int tw, int th, int* recs, uint32_t* keys,
+                       cudaStream_t s);
 // vis: [n * V] bytes, 1 where (g, v) is visible; counts: visible views per Gaussian.
 void launch_count_visible(const SceneArgs& sc, const DevCam* cams, int V, int tw, int th, int* counts, uint8_t* vis,
                           cudaStream_t s);

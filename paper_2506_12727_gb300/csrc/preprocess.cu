@@ -257,6 +257,28 @@ __global__ void __launch_bounds__(256) count_visible_kernel(SceneArgs sc, const 
     counts[g] = cnt;
 }
 
+// Participation pre-count for sizing: per Gaussian, the visible views and the
+// tiles they cover (the same projection as the render, so the totals are the
+// render's record and key counts exactly).
+__global__ void __launch_bounds__(256) count_keys_kernel(SceneArgs sc, const DevCam* __restrict__ cams, int V, int tw,
+                                                         int th, int* __restrict__ recs,
+                                                         uint32_t* __restrict__ keys) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= sc.n) return;
+    Gauss G;
+    load_gauss(sc, g, G, true);
+    int r = 0;
+    unsigned long long k = 0;
+    for (int v = 0; v < V; v++) {
+        Proj P;
+        if (!project(G, cams[v], tw, th, P)) continue;
+        r++;
+        k += (unsigned long long)((P.rect.z - P.rect.x) * (P.rect.w - P.rect.y));
+    }
+    recs[g] = r;
+    keys[g] = (uint32_t)(k < 0xffffffffull ? k : 0xffffffffull);
+}
+
 template <int DEG>
 __global__ void __launch_bounds__(256) preprocess_kernel(SceneArgs sc, const DevCam* __restrict__ cams, int V, int tw,
                                                          int th, const uint8_t* __restrict__ vis, RecordArgs rec,
@@ -511,6 +533,13 @@ void upload_cams(const DevCam* host, int V, DevCam* dst, cudaStream_t s) {
         upload_cams_kernel<<<1, kCamChunk, 0, s>>>(chunk, cnt, dst + start);
         note_launches(1);
     }
+}
+
+void launch_count_keys(const SceneArgs& sc, const DevCam* cams, int V, int tw, int th, int* recs, uint32_t* keys,
+                       cudaStream_t s) {
+    if (sc.n == 0) return;
+    count_keys_kernel<<<blocks_for(sc.n, 256), 256, 0, s>>>(sc, cams, V, tw, th, recs, keys);
+    note_launches(1);
 }
 
 void launch_count_visible(const SceneArgs& sc, const DevCam* cams, int V, int tw, int th, int* counts,

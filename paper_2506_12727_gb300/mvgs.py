@@ -92,7 +92,8 @@ EXPORTS = ["mvgs_render_layout", "mvgs_render_views", "mvgs_render_views_backwar
            "mvgs_partial_samples_workspace_size", "mvgs_partial_samples", "mvgs_render_views_sampled",
            "mvgs_render_views_sampled_backward", "mvgs_merge_workspace_size", "mvgs_merge_views",
            "mvgs_split_merged_grad", "mvgs_dssim3d_workspace_size", "mvgs_dssim3d_loss",
-           "mvgs_densify_workspace_size", "mvgs_densify", "mvgs_densify_carry", "mvgs_adam_step"]
+           "mvgs_densify_workspace_size", "mvgs_densify", "mvgs_densify_carry", "mvgs_adam_step",
+           "mvgs_count_workspace_size", "mvgs_count_views"]
 
 
 def load_library(path: str | None = None):
@@ -118,6 +119,10 @@ def load_library(path: str | None = None):
     lib.mvgs_dssim3d_workspace_size.argtypes = [P, I32]
     lib.mvgs_dssim3d_workspace_size.restype = SZ
     lib.mvgs_dssim3d_loss.argtypes = [P, P, P, P, P, I32, ctypes.c_float, P, P, P, SZ, P]
+    lib.mvgs_count_workspace_size.argtypes = [I64, I32]
+    lib.mvgs_count_workspace_size.restype = SZ
+    lib.mvgs_count_views.argtypes = [P, P, I32, P, P, P, SZ, P]
+    lib.mvgs_count_views.restype = ctypes.c_int
     lib.mvgs_densify_workspace_size.argtypes = [I64]
     lib.mvgs_densify_workspace_size.restype = SZ
     lib.mvgs_densify.argtypes = [P, P, P, P, P, P, I64, P, P, P, P, P, P, P, P, P, SZ, P]
@@ -249,6 +254,15 @@ class SampleSet:
         """The pixel indices as int64 (0 .. tile_w * tile_h - 1)."""
         n = int(self.offsets[-1])
         return self.pixels[:n].to(torch.int64) & 0xFFFF
+
+
+def count_views(scene_c, cams_c, cfg, device="cuda", stream=None) -> Capacity:
+    """mvgs_count_views: the exact records and keys a render of these views needs."""
+    ws = torch.empty(int(_lib.mvgs_count_workspace_size(scene_c.n, len(cams_c))), dtype=torch.uint8, device=device)
+    needed = Capacity()
+    _check(_lib.mvgs_count_views(ctypes.byref(scene_c), cams_c, len(cams_c), ctypes.byref(cfg), ctypes.byref(needed),
+                                 _ptr(ws), ws.numel(), _stream(stream)))
+    return needed
 
 
 def sampling(group: int, seed: int, cell=(1, 1)) -> Sampling:
@@ -446,6 +460,14 @@ class Rasterizer:
 
     def reserve(self, n, records, keys):
         self._ensure(n, records, keys)
+
+    def reserve_for(self, scene_c, extra=1.0, stream=None) -> Capacity:
+        """Sizes the buffers for this scene from the exact pre-count (times
+        `extra` on top of the rasterizer's headroom, for parameters that will
+        move, e.g. a captured training step); returns the counts."""
+        need = count_views(scene_c, self.cams_c, self.cfg, self.device, stream)
+        self.reserve(scene_c.n, int(need.records * extra), int(need.keys * extra))
+        return need
 
     def held_bytes(self) -> int:
         return 0 if self.state is None else self.state.numel() + self.workspace.numel()

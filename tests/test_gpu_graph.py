@@ -128,3 +128,20 @@ def test_captured_step_replays_on_new_parameters(world, cuda_lib):
     for k in PARAMS:
         e = g2[k].cpu().numpy()
         assert_close_frac(got_g[k].cpu().numpy(), e, 1e-3, 1e-5 * np.abs(e).max(), k)
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (16, 64), (8, 8)])
+def test_precount_equals_render_counts(world, cuda_lib, tile):
+    cams, params = world["cams"], world["params"]
+    sc = cuda_lib.make_scene(params, 3)
+    rz = cuda_lib.Rasterizer(cams, tile=tile)
+    need = cuda_lib.count_views(sc, rz.cams_c, rz.cfg)
+    rz.forward(sc)
+    torch.cuda.synchronize()
+    assert (need.records, need.keys) == (int(rz.needed.records), int(rz.needed.keys))
+    # a capturable rasterizer sized from the pre-count fits
+    rc = cuda_lib.Rasterizer(cams, tile=tile, capturable=True, headroom=1.0)
+    rc.reserve_for(sc)
+    rc.forward(sc)
+    torch.cuda.synchronize()
+    assert rc.fits()
