@@ -257,6 +257,30 @@ __global__ void __launch_bounds__(256) count_visible_kernel(SceneArgs sc, const 
     counts[g] = cnt;
 }
 
+// SH coefficients of one Gaussian ([NK, 3], channel-minor) read as float4
+// vectors when the row allows it (12 instead of 48 loads at degree 3), else
+// one by one.  f(e, value) receives flat element e = 3 k + ch.
+template <int NK, class F>
+__device__ __forceinline__ void for_each_sh(const float* __restrict__ row, bool vec_ok, F f) {
+    constexpr int E = NK * 3;
+    if constexpr (E % 4 == 0) {
+        if (vec_ok) {
+            const float4* r4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+            for (int q = 0; q < E / 4; q++) {
+                const float4 v = __ldg(r4 + q);
+                f(4 * q, v.x);
+                f(4 * q + 1, v.y);
+                f(4 * q + 2, v.z);
+                f(4 * q + 3, v.w);
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < E; e++) f(e, __ldg(row + e));
+}
+
 // Participation pre-count for sizing: per Gaussian, the visible views and the
 // tiles they cover (the same projection as the render, so the totals are the
 // render's record and key counts exactly).
@@ -292,6 +316,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneArgs sc, const Dev
     load_gauss(sc, g, G, true);
     long long r = rec.rec_off[g];
     const float* shg = sc.sh + (size_t)g * NK * 3;
+    const bool sh_vec = (reinterpret_cast<uintptr_t>(sc.sh) & 15) == 0;  // rows of 48 floats stay 16-byte aligned
     for (int v = 0; v < V; v++) {
         if (!vis[g * V + v]) continue;
         if (r >= rec.cap) break;  // capturable mode past its record capacity (reported through the counts)
@@ -310,15 +335,12 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneArgs sc, const Dev
         dx *= il; dy *= il; dz *= il;
         float Y[NK];
         sh_basis<DEG>(dx, dy, dz, Y);
-        float rgb[3];
+        float rgb[3] = {0.5f, 0.5f, 0.5f};
         int clamp = 0;
+        for_each_sh<NK>(shg, sh_vec, [&](int e, float c) { rgb[e % 3] += Y[e / 3] * c; });
 #pragma unroll
         for (int ch = 0; ch < 3; ch++) {
-            float acc = 0.5f;
-#pragma unroll
-            for (int k = 0; k < NK; k++) acc += Y[k] * shg[3 * k + ch];
-            if (acc < 0.f) { clamp |= 1 << ch; acc = 0.f; }
-            rgb[ch] = acc;
+            if (rgb[ch] < 0.f) { clamp |= 1 << ch; rgb[ch] = 0.f; }
         }
         rec.rgb_r[r] = make_float4(rgb[0], rgb[1], rgb[2], (float)P.radius);
         rec.clamp[r] = clamp;
@@ -341,7 +363,7 @@ __global__ void zero_kernel(float4* __restrict__ p, size_t n4) {
 // and sums the view contributions in registers, so every parameter gradient
 // is written exactly once, without atomics.
 template <int DEG>
-__global__ void __launch_bounds__(128) preprocess_backward_kernel(SceneArgs sc, const DevCam* __restrict__ cams,
+__global__ void __launch_bounds__(128, 3) preprocess_backward_kernel(SceneArgs sc, const DevCam* __restrict__ cams,
                                                                   RecordArgs rec, const float* __restrict__ rg,
                                                                   const double* __restrict__ rc,
                                                                   float* __restrict__ g_means,
@@ -357,6 +379,7 @@ __global__ void __launch_bounds__(128) preprocess_backward_kernel(SceneArgs sc, 
     Gauss G;
     load_gauss(sc, g, G, true);
     const float* shg = sc.sh + (size_t)g * NK * 3;
+    const bool sh_vec = (reinterpret_cast<uintptr_t>(sc.sh) & 15) == 0;  // rows of 48 floats stay 16-byte aligned
     float gmu[3] = {0.f, 0.f, 0.f};
     float gS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma, symmetric (xx, xy, xz, yy, yz, zz)
     float go = 0.f;
@@ -450,14 +473,11 @@ __global__ void __launch_bounds__(128) preprocess_backward_kernel(SceneArgs sc, 
         float wk[NK];
 #pragma unroll
         for (int k = 0; k < NK; k++) {
-            float acc = 0.f;
+            wk[k] = 0.f;
 #pragma unroll
-            for (int ch = 0; ch < 3; ch++) {
-                gsh[3 * k + ch] += Y[k] * grgb[ch];
-                acc += shg[3 * k + ch] * grgb[ch];
-            }
-            wk[k] = acc;
+            for (int ch = 0; ch < 3; ch++) gsh[3 * k + ch] += Y[k] * grgb[ch];
         }
+        for_each_sh<NK>(shg, sh_vec, [&](int e, float c) { wk[e / 3] += c * grgb[e % 3]; });
         const float3 gd = sh_basis_grad<DEG>(dx, dy, dz, wk);
         const float dd = gd.x * dx + gd.y * dy + gd.z * dz;
         gmu[0] += (gd.x - dx * dd) * il;
@@ -468,8 +488,20 @@ __global__ void __launch_bounds__(128) preprocess_backward_kernel(SceneArgs sc, 
 #pragma unroll
     for (int j = 0; j < 3; j++) g_means[3 * g + j] = gmu[j];
     g_logits[g] = go * G.o * (1.f - G.o);
+    float* gshg = g_sh + (size_t)g * NK * 3;
+    if constexpr ((NK * 3) % 4 == 0) {
+        if ((reinterpret_cast<uintptr_t>(g_sh) & 15) == 0) {
 #pragma unroll
-    for (int i = 0; i < NK * 3; i++) g_sh[(size_t)g * NK * 3 + i] = gsh[i];
+            for (int q = 0; q < NK * 3 / 4; q++)
+                reinterpret_cast<float4*>(gshg)[q] = make_float4(gsh[4 * q], gsh[4 * q + 1], gsh[4 * q + 2], gsh[4 * q + 3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < NK * 3; i++) gshg[i] = gsh[i];
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NK * 3; i++) gshg[i] = gsh[i];
+    }
     // Sigma = M M^T, M = R diag(s): dL/dM = 2 dL/dSigma M
     float gM[9];
 #pragma unroll
