@@ -128,7 +128,7 @@ def run_ours(args, rank, world):
     import torch
     from paper_2506_12727_gb300 import build as lib_build
     lib_build.build()
-    from paper_2506_12727_gb300 import mvgs
+    from paper_2506_12727_gb300 import mvgs, shard
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
@@ -172,6 +172,10 @@ def run_ours(args, rank, world):
             e1 = torch.empty(int(R * 1.2) + 16, device=dev)
         rast.backward(scene_c, dimg_, grads, gm2d, e1)
         mvgs.adc_accumulate(rast.state, n, gm2d, e1, *acc)
+        if dist:
+            # data parallel over ranks: each renders its own batch of views
+            # against a replica; gradients and ADC statistics are summed
+            shard.reduce_step(grads, acc)
 
     def timed(fn, steps, warmup, profile=False):
         for _ in range(warmup):
@@ -364,7 +368,8 @@ def run_ours(args, rank, world):
                    "pixels_per_thread": args.ppt or "auto", "autotune_ms": tuning,
                    "records": needed[0], "keys": needed[1],
                    "l2": "512 MB buffer written between timed steps (L2 is 129 MB); per-step working set > 1 GB",
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": (f"dp{world}: a batch of {V} views per rank, gradient and ADC all-reduce"
+                                   if world > 1 else "single")},
         "e2e": None if ms_e2e is None else {"value": V * world / (ms_e2e / 1e3), "unit": "views/s",
                                             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(round(launches_per_step * args.steps)),
