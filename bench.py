@@ -482,6 +482,14 @@ def stage_work(rz, needed, V, pixels):
     }, blended
 
 
+# DRAM bytes (read + write) per blended pair of the blend kernels, from the ncu
+# --set full capture of one view of this scene (profiles/blend_kernels_
+# multiview_500k_1x1264x832_16x64.md: forward 22.62 MB, backward 50.35 MB over
+# 103,536,139 blended pairs); a full launch's traffic is taken in proportion
+# to its blended pairs.  Valid for the kernels as captured.
+DRAM_BYTES_PER_BLENDED = {"blend_forward": 22.622464e6 / 103536139, "blend_backward": 50.347776e6 / 103536139}
+
+
 def roofline(stages, args, needed, rz, clk, V, pixels):
     """Per-stage achieved / peak, and the dominant stage's entry."""
     if not stages:
@@ -512,6 +520,10 @@ def roofline(stages, args, needed, rz, clk, V, pixels):
     d.pop("ms")
     d["kernel"] = dom
     d["traffic"] = None
+    if dom in DRAM_BYTES_PER_BLENDED and blended:
+        d["traffic"] = int(DRAM_BYTES_PER_BLENDED[dom] * blended)
+        d["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the one-view capture, "
+                               "scaled by blended pairs")
     if d["bound"] == "alu":
         per = FWD_FLOP_PER_BLENDED if dom == "blend_forward" else BWD_FLOP_PER_BLENDED
         d["algorithmic"] = f"{per} FLOP x {blended} blended (pixel, Gaussian) pairs per launch"
