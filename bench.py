@@ -327,6 +327,40 @@ def run_ours(args, rank, world):
             modes[name] = {"render_fwd_bwd_ms": round(ms_m, 4),
                            "blend_forward_ms": round(st_m.get("blend_forward", (0, 0))[0] / nst, 4),
                            "blend_backward_ms": round(st_m.get("blend_backward", (0, 0))[0] / nst, 4)}
+        # the whole partial training step of Sec. 5.1 (one merged image per
+        # iteration): sampled render with depth, merge, 3D distance-aware
+        # D-SSIM + L1, split, sampled backward, ADC
+        if (cams.width == cams.width[0]).all() and (cams.height == cams.height[0]).all():
+            H0, W0 = int(cams.height[0]), int(cams.width[0])
+            mimg = torch.empty(3 * H0 * W0, device=dev)
+            mtgt, pts = torch.empty_like(mimg), torch.empty_like(mimg)
+            sig = torch.empty(H0 * W0, device=dev)
+            mhw = np.array([[H0, W0]], np.int32)
+            mloss = torch.empty(1, device=dev)
+            dm = torch.empty_like(mimg)
+            ws3 = torch.empty(mvgs.dssim3d_workspace_size(mhw), dtype=torch.uint8, device=dev)
+            pimg = torch.zeros(3 * rz.pixels, device=dev)
+            pd = torch.empty_like(pimg)
+            cell = rz.strip_cell()
+
+            def partial_train_step():
+                rz.forward(sc, images=pimg, samples=ss_strip, depth=True)
+                rec = rz.records()
+                mvgs.merge_views(rz.cams_c, V, 11, pimg, tgt, rec["depth_acc"], rec["final_T"], mimg, mtgt, pts,
+                                 sig, cell=cell)
+                mvgs.dssim3d_loss(mimg, mtgt, pts, sig, mhw, LAMBDA, mloss, dm, ws3)
+                mvgs.split_merged_grad(rz.cams_c, V, 11, dm, pd, cell=cell)
+                R = int(rz.needed.records)
+                gm_p = torch.empty(max(R, 1), 2, device=dev)
+                e1_p = torch.empty(max(R, 1), device=dev)
+                rz.backward(sc, pd, grads, gm_p, e1_p, samples=ss_strip)
+                mvgs.adc_accumulate(rz.state, n, gm_p, e1_p, *acc)
+
+            ms_pt, st_pt = timed(partial_train_step, max(3, args.steps // 2), 2, profile=True)
+            nst = max(3, args.steps // 2)
+            modes["train_step_partial_3d_dssim"] = {
+                "ms": round(ms_pt, 4), "merged_images_per_s": 1e3 / ms_pt,
+                "stages_ms": {k: round(v[0] / nst, 4) for k, v in st_pt.items() if v[1]}}
         partial = {"group": V, "sampled_pixels": int(ss.offsets[-1].item()), "pixels": rz.pixels,
                    "sampling": "per pixel (1x1 cells); strip cells: %dx%d" % rz.strip_cell(),
                    "modes": modes,
