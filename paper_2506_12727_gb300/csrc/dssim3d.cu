@@ -16,7 +16,7 @@
 //         itself); SSIM with K* in place of the 2D window, C1 = 0.01^2,
 //         C2 = 0.03^2; L_m = (1 - lambda) mean|I - I*| + lambda (1 - mean SSIM),
 //         the weights held constant.
-//         Kernel 1 (per 16x16 block, halo 26x26 in shared memory) forms the
+//         Kernel 1 (per 32x8 block, halo 42x18 in shared memory) forms the
 //         weights, the moments, SSIM and, per centre p and channel, the
 //         coefficients A_p, B_p, C_p / Z_p of dSSIM_p/dI1(q) = w_pq (A + 2 B
 //         I1(q) + C I2(q)) / Z_p; kernel 2 gathers them back per pixel q over
@@ -31,9 +31,11 @@
 namespace mvgs {
 namespace {
 
-constexpr int TS = 16;
+// 32 x 8 pixels per block: a warp holds one row of 32 pixels, so its
+// shared-memory reads of a neighbour offset fall in 32 different banks
+constexpr int TSX = 32, TSY = 8;
 constexpr int RAD = 5;
-constexpr int HS = TS + 2 * RAD;  // 26
+constexpr int HSX = TSX + 2 * RAD, HSY = TSY + 2 * RAD;  // 42 x 18 staged
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
 constexpr int kMaxImages = 64;
@@ -75,8 +77,8 @@ __device__ __forceinline__ Blk block_of(const Images& im) {
     const long long t = blockIdx.x - im.blk[b.i];
     b.H = im.H[b.i];
     b.W = im.W[b.i];
-    b.x0 = (int)(t % im.tiles_x[b.i]) * TS;
-    b.y0 = (int)(t / im.tiles_x[b.i]) * TS;
+    b.x0 = (int)(t % im.tiles_x[b.i]) * TSX;
+    b.y0 = (int)(t / im.tiles_x[b.i]) * TSY;
     b.pix = im.pix[b.i];
     return b;
 }
@@ -87,12 +89,12 @@ __global__ void __launch_bounds__(256) dssim3d_forward_kernel(Images im, long lo
                                                              const float* __restrict__ sig,
                                                              float* __restrict__ coef, float2* __restrict__ bsum,
                                                              long long blk_offset) {
-    __shared__ float sX[3][HS][HS + 1], sS[HS][HS + 1], s1[3][HS][HS + 1], s2[3][HS][HS + 1];
+    __shared__ float sX[3][HSY][HSX + 1], sS[HSY][HSX + 1], s1[3][HSY][HSX + 1], s2[3][HSY][HSX + 1];
     __shared__ float red[2][8];
     const Blk b = block_of(im);
     const long long HW = (long long)b.H * b.W;
-    for (int k = threadIdx.x; k < HS * HS; k += blockDim.x) {
-        const int r = k / HS, c = k % HS;
+    for (int k = threadIdx.x; k < HSX * HSY; k += blockDim.x) {
+        const int r = k / HSX, c = k % HSX;
         const int y = b.y0 + r - RAD, x = b.x0 + c - RAD;
         const bool in = x >= 0 && y >= 0 && x < b.W && y < b.H;
         const long long o = (long long)y * b.W + x;
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(256) dssim3d_forward_kernel(Images im, long lo
         }
     }
     __syncthreads();
-    const int r = threadIdx.x / TS + RAD, c = threadIdx.x % TS + RAD;
+    const int r = threadIdx.x / TSX + RAD, c = threadIdx.x % TSX + RAD;
     const int x = b.x0 + c - RAD, y = b.y0 + r - RAD;
     float ssim = 0.f, l1 = 0.f;
     if (x < b.W && y < b.H) {
@@ -178,11 +180,11 @@ __global__ void __launch_bounds__(256) dssim3d_backward_kernel(Images im, long l
                                                               const float* __restrict__ sig,
                                                               const float* __restrict__ coef, float lambda,
                                                               float inv_images, float* __restrict__ dimg) {
-    __shared__ float sX[3][HS][HS + 1], sS[HS][HS + 1], sC[9][HS][HS + 1];
+    __shared__ float sX[3][HSY][HSX + 1], sS[HSY][HSX + 1], sC[9][HSY][HSX + 1];
     const Blk b = block_of(im);
     const long long HW = (long long)b.H * b.W;
-    for (int k = threadIdx.x; k < HS * HS; k += blockDim.x) {
-        const int r = k / HS, c = k % HS;
+    for (int k = threadIdx.x; k < HSX * HSY; k += blockDim.x) {
+        const int r = k / HSX, c = k % HSX;
         const int y = b.y0 + r - RAD, x = b.x0 + c - RAD;
         const bool in = x >= 0 && y >= 0 && x < b.W && y < b.H;
         const long long o = (long long)y * b.W + x;
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(256) dssim3d_backward_kernel(Images im, long l
         for (int j = 0; j < 9; j++) sC[j][r][c] = in ? coef[j * P + b.pix + o] : 0.f;
     }
     __syncthreads();
-    const int r = threadIdx.x / TS + RAD, c = threadIdx.x % TS + RAD;
+    const int r = threadIdx.x / TSX + RAD, c = threadIdx.x % TSX + RAD;
     const int x = b.x0 + c - RAD, y = b.y0 + r - RAD;
     if (x >= b.W || y >= b.H) return;
     const float qx = sX[0][r][c], qy = sX[1][r][c], qz = sX[2][r][c], sq = sS[r][c];
@@ -320,11 +322,11 @@ Images make_images(const int* hw, int first, int count) {
         const int H = hw[2 * (first + i)], W = hw[2 * (first + i) + 1];
         im.H[i] = H;
         im.W[i] = W;
-        im.tiles_x[i] = (W + TS - 1) / TS;
+        im.tiles_x[i] = (W + TSX - 1) / TSX;
         im.pix[i] = pix;
         im.blk[i] = blk;
         pix += (long long)H * W;
-        blk += (long long)im.tiles_x[i] * ((H + TS - 1) / TS);
+        blk += (long long)im.tiles_x[i] * ((H + TSY - 1) / TSY);
     }
     im.blk[count] = blk;
     return im;
@@ -338,7 +340,7 @@ size_t dssim3d_temp_bytes(const int* hw, int M) {
     long long P = 0, blocks = 0;
     for (int i = 0; i < M; i++) {
         P += (long long)hw[2 * i] * hw[2 * i + 1];
-        blocks += (long long)((hw[2 * i + 1] + TS - 1) / TS) * ((hw[2 * i] + TS - 1) / TS);
+        blocks += (long long)((hw[2 * i + 1] + TSX - 1) / TSX) * ((hw[2 * i] + TSY - 1) / TSY);
     }
     return align256(9 * (size_t)P * sizeof(float)) + align256((size_t)blocks * sizeof(float2));
 }
