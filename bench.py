@@ -598,11 +598,33 @@ def oracle_sample(workload, view=0, window=None):
     return dt, frac
 
 
+def _band_sample(args):
+    workload, band = args
+    return oracle_sample(workload, window=np.array([band]))
+
+
 def cpu_baseline(workload):
+    """The oracle on the host: one thread on view 0, and all cores on view 0 cut
+    into one horizontal band per core (spawned processes; each band's loss is
+    the band's own, which moves no work).  The all-cores figure is the main
+    value."""
+    import multiprocessing as mpr
     dt, frac = oracle_sample(workload)
-    return {"value": frac / dt, "unit": "views/s", "cores": 1, "kind": "oracle",
-            "sample": f"view 0 of {workload}, full resolution, forward + loss + backward, one thread",
-            "seconds": dt}
+    single = {"value": frac / dt, "cores": 1, "seconds": dt,
+              "sample": f"view 0 of {workload}, full resolution, forward + loss + backward, one thread"}
+    _, cams, _ = synth.workload(workload)
+    W, H = int(cams.width[0]), int(cams.height[0])
+    cores = max(1, min(os.cpu_count() or 1, H // 16))
+    bands = [[0, H * i // cores, W, H * (i + 1) // cores] for i in range(cores)]
+    t0 = time.perf_counter()
+    with mpr.get_context("spawn").Pool(cores) as pool:
+        parts = pool.map(_band_sample, [(workload, b) for b in bands])
+    wall = time.perf_counter() - t0
+    covered = sum(f for _, f in parts)
+    return {"value": covered / wall, "unit": "views/s", "cores": cores, "kind": "oracle",
+            "sample": f"view 0 of {workload} in {cores} row bands, one process per core (spawned), "
+                      "forward + loss + backward; wall time includes the processes' start",
+            "seconds": wall, "single_thread": single}
 
 
 def run_reference(args, rank, world):
