@@ -369,6 +369,40 @@ def run_ours(args, rank, world):
                        max(1e-9, modes["thread_efficient"]["blend_forward_ms"] +
                            modes["thread_efficient"]["blend_backward_ms"])}
 
+    # ---- training-loop kernels: Adam over every parameter, one densification step ----
+    training = None
+    if not args.no_partial:
+        m_st = {k: torch.zeros_like(v) for k, v in params.items()}
+        v_st = {k: torch.zeros_like(v) for k, v in params.items()}
+        p_copy = {k: v.clone() for k, v in params.items()}
+        t_adam = [0]
+
+        def adam_all():
+            t_adam[0] += 1
+            for k in p_copy:
+                mvgs.adam_step(p_copy[k], grads[k], m_st[k], v_st[k], 1e-3, t_adam[0])
+        ms_adam, _ = timed(adam_all, max(3, args.steps // 2), 2)
+        elems = sum(v.numel() for v in params.values())
+        adam_bytes = 28 * elems  # read p, g, m, v; write p, m, v (float32)
+        z = torch.randn(n, 2, 3, device=dev)
+        t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0e.record()
+        new_p, _, _, _ = mvgs.densify(p_copy, scene.sh_degree, acc[0], acc[1], acc[2], z, 2e-4, 2e-4,
+                                      float(np.log(0.02 / 0.98)), float(np.log(0.01)))
+        t1e.record()
+        torch.cuda.synchronize()
+        peaks, _ = _peaks()
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        training = {"adam_ms": round(ms_adam, 4),
+                    "adam_roofline": {"bound": "hbm", "achieved": round(adam_bytes / (ms_adam / 1e3) / 1e9, 1),
+                                      "peak": hbm, "unit": "GB/s",
+                                      "frac": round(adam_bytes / (ms_adam / 1e3) / 1e9 / hbm, 4),
+                                      "algorithmic": f"28 B x {elems} parameters"},
+                    "densify_ms": round(t0e.elapsed_time(t1e), 3),
+                    "densify_gaussians": [n, int(new_p["means"].shape[0])],
+                    "densify_note": "includes one count read-back and the allocation of the outputs"}
+        del m_st, v_st, p_copy, new_p
+
     # ---- serving loop: resident 2M SH-3 scene, Poisson arrivals ----
     serving = None
     if not args.no_serve and rank == 0:
@@ -410,6 +444,7 @@ def run_ours(args, rank, world):
         "per_view_loop": loop,
         "cuda_graph": graph,
         "partial_rendering": partial,
+        "training_kernels": training,
         "serving": serving,
         "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in (stages or {}).items() if v[1]},
         "roofline": roof,

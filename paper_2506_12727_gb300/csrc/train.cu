@@ -108,6 +108,32 @@ __global__ void adam_kernel(long long count, float* __restrict__ p, const float*
     }
 }
 
+// The same update on float4 vectors (count4 = count / 4, all pointers 16-byte
+// aligned); the caller handles a tail of count % 4 elements with adam_kernel.
+__device__ __forceinline__ void adam1(float& p, float g, float& m, float& v, float lr, float b1, float b2, float eps,
+                                      float c1, float c2) {
+    m = b1 * m + (1.f - b1) * g;
+    v = b2 * v + (1.f - b2) * g * g;
+    p -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+}
+
+__global__ void adam4_kernel(long long count4, float4* __restrict__ p, const float4* __restrict__ g,
+                             float4* __restrict__ m, float4* __restrict__ v, float lr, float b1, float b2, float eps,
+                             float c1, float c2) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count4;
+         i += (long long)gridDim.x * blockDim.x) {
+        float4 pp = p[i], mm = m[i], vv = v[i];
+        const float4 gg = g[i];
+        adam1(pp.x, gg.x, mm.x, vv.x, lr, b1, b2, eps, c1, c2);
+        adam1(pp.y, gg.y, mm.y, vv.y, lr, b1, b2, eps, c1, c2);
+        adam1(pp.z, gg.z, mm.z, vv.z, lr, b1, b2, eps, c1, c2);
+        adam1(pp.w, gg.w, mm.w, vv.w, lr, b1, b2, eps, c1, c2);
+        p[i] = pp;
+        m[i] = mm;
+        v[i] = vv;
+    }
+}
+
 }  // namespace
 
 size_t densify_temp_bytes(long long n) {
@@ -154,10 +180,27 @@ void launch_adam(long long count, float* p, const float* g, float* m, float* v, 
                  float eps, int step, cudaStream_t s) {
     if (count <= 0) return;
     const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
-    long long blocks = (count + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    adam_kernel<<<(unsigned)blocks, 256, 0, s>>>(count, p, g, m, v, lr, b1, b2, eps, c1, c2);
-    note_launches(1);
+    const bool aligned = ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(g) |
+                           reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v)) & 15) == 0;
+    long long head = 0;
+    if (aligned && count >= 4) {
+        const long long c4 = count / 4;
+        long long blocks = (c4 + 255) / 256;
+        if (blocks > 152 * 8) blocks = 152 * 8;
+        adam4_kernel<<<(unsigned)blocks, 256, 0, s>>>(c4, reinterpret_cast<float4*>(p),
+                                                      reinterpret_cast<const float4*>(g),
+                                                      reinterpret_cast<float4*>(m), reinterpret_cast<float4*>(v),
+                                                      lr, b1, b2, eps, c1, c2);
+        note_launches(1);
+        head = 4 * c4;
+    }
+    if (head < count) {
+        long long blocks = (count - head + 255) / 256;
+        if (blocks > 152 * 16) blocks = 152 * 16;
+        adam_kernel<<<(unsigned)blocks, 256, 0, s>>>(count - head, p + head, g + head, m + head, v + head, lr, b1,
+                                                     b2, eps, c1, c2);
+        note_launches(1);
+    }
 }
 
 }  // namespace mvgs
