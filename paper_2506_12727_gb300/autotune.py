@@ -13,8 +13,8 @@ import torch
 from . import mvgs
 
 CANDIDATES = (
-    ((16, 16), 0), ((16, 32), 0), ((16, 32), 2), ((32, 32), 0), ((32, 32), 2), ((16, 64), 0), ((16, 64), 2),
-    ((16, 64), 1), ((32, 64), 0), ((32, 64), 2), ((32, 16), 0),
+    ((16, 16), 0), ((16, 32), 0), ((16, 32), 2), ((32, 32), 0), ((16, 64), 0), ((16, 64), 2), ((32, 64), 0),
+    ((32, 16), 0),
 )
 
 _cache: dict = {}
