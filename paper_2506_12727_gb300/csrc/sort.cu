@@ -340,6 +340,7 @@ __device__ __forceinline__ uint64_t dup_record(const DupSrc& src, const int* s_o
 }
 
 constexpr int DUP_ITEMS = RS_ITEMS;  // consecutive entries per thread
+constexpr int DUP_MAXR = 1024;       // records a block stages in shared memory
 
 // first[b] = the record holding entry b * TILE, for every radix block b:
 // each record fills the blocks whose first entry it holds, so no block has to
@@ -364,6 +365,12 @@ __global__ void __launch_bounds__(RS_THREADS) dup_hist_kernel(DupSrc src, const 
                                                              uint32_t* __restrict__ counts, uint32_t nblocks) {
     __shared__ uint32_t hist[RS_WARPS * 256];
     __shared__ int s_off[RS_TILE + 2];
+    // the block's records, gathered once by all threads together (their
+    // loads are independent, so they are all in flight at once) instead of
+    // one dependent chain order -> rect, view -> camera per thread and record
+    __shared__ uint32_t s_rec[DUP_MAXR], s_base[DUP_MAXR];
+    __shared__ short4 s_rect[DUP_MAXR];
+    __shared__ int s_tx[DUP_MAXR];
     const uint64_t K = Kc.get();
     const uint64_t k0 = (uint64_t)blockIdx.x * RS_TILE;
     if (k0 >= K) {  // a block past the entries (capturable mode): empty histogram
@@ -379,7 +386,36 @@ __global__ void __launch_bounds__(RS_THREADS) dup_hist_kernel(DupSrc src, const 
     const uint64_t rhi = first_rec[blockIdx.x + 1];
     const int nr = rhi - rlo + 1 <= (uint64_t)RS_TILE ? (int)(rhi - rlo + 1) : -1;
     for (int i = threadIdx.x; i <= nr; i += RS_THREADS) s_off[i] = (int)((long long)src.off[rlo + i] - (long long)k0);
+    const bool staged = nr > 0 && nr <= DUP_MAXR;
+    if (staged) {
+        for (int i = threadIdx.x; i < nr; i += RS_THREADS) {
+            const uint32_t rec = src.order[rlo + i];
+            const DevCam& c = src.cams[src.rec_v[rec]];
+            s_rec[i] = rec;
+            s_rect[i] = src.rect[rec];
+            s_base[i] = (uint32_t)c.tile_base;
+            s_tx[i] = c.tiles_x;
+        }
+    }
     __syncthreads();
+    // record rr: id, rectangle, view tile base, tiles per row, end of its entries
+    auto load = [&](uint64_t rr, uint32_t& rec, short4& rc, long long& base, int& txs, uint64_t& rend) {
+        if (staged) {
+            const int li = (int)(rr - rlo);
+            rec = s_rec[li];
+            rc = s_rect[li];
+            base = s_base[li];
+            txs = s_tx[li];
+            rend = k0 + (uint64_t)(long long)s_off[li + 1];
+        } else {
+            rec = src.order[rr];
+            rc = src.rect[rec];
+            const DevCam& c = src.cams[src.rec_v[rec]];
+            base = c.tile_base;
+            txs = c.tiles_x;
+            rend = src.off[rr + 1];
+        }
+    };
     uint32_t* wh = hist + (threadIdx.x >> 5) * 256;
     const uint64_t first = k0 + (uint64_t)threadIdx.x * DUP_ITEMS;
     uint32_t kk[DUP_ITEMS], vv[DUP_ITEMS];
@@ -387,12 +423,15 @@ __global__ void __launch_bounds__(RS_THREADS) dup_hist_kernel(DupSrc src, const 
     for (int i = 0; i < DUP_ITEMS; i++) kk[i] = vv[i] = 0u;
     if (first < K) {
         uint64_t r = dup_record(src, s_off, rlo, nr, k0, first);
-        uint64_t rend = src.off[r + 1];
-        uint32_t rec = src.order[r];
-        short4 rc = src.rect[rec];
-        const DevCam* cam = &src.cams[src.rec_v[rec]];
+        uint64_t rend;
+        uint32_t rec;
+        short4 rc;
+        long long base;
+        int txs;
+        load(r, rec, rc, base, txs, rend);
         int w = max(rc.z - rc.x, 1);
-        const uint32_t j = (uint32_t)(first - src.off[r]);
+        const uint64_t rstart = staged ? k0 + (uint64_t)(long long)s_off[r - rlo] : src.off[r];
+        const uint32_t j = (uint32_t)(first - rstart);
         int tx = rc.x + (int)(j % (uint32_t)w), ty = rc.y + (int)(j / (uint32_t)w);
 #pragma unroll
         for (int i = 0; i < DUP_ITEMS; i++) {
@@ -400,15 +439,12 @@ __global__ void __launch_bounds__(RS_THREADS) dup_hist_kernel(DupSrc src, const 
             if (idx < K) {
                 while (idx >= rend) {  // next record (skipping any without tiles)
                     r++;
-                    rend = src.off[r + 1];
-                    rec = src.order[r];
-                    rc = src.rect[rec];
-                    cam = &src.cams[src.rec_v[rec]];
+                    load(r, rec, rc, base, txs, rend);
                     w = max(rc.z - rc.x, 1);
                     tx = rc.x;
                     ty = rc.y;
                 }
-                const long long t = cam->tile_base + (long long)ty * cam->tiles_x + tx;
+                const long long t = base + (long long)ty * txs + tx;
                 const uint32_t key = (uint32_t)(t < (long long)src.tiles ? t : (long long)src.tiles - 1);
                 kk[i] = key;
                 vv[i] = rec;
