@@ -5,8 +5,8 @@
 // Gaussian kernel; D-SSIM = 1 - SSIM.  Window 11x11, sigma 1.5, normalised
 // to sum 1 and applied separably; zero padding; C1 = 0.01^2, C2 = 0.03^2.
 //
-// Kernel 1 computes, per 32x16 output tile of one channel plane, the five
-// blurred moments from a 42x26 staged input, the SSIM map, and the three
+// Kernel 1 computes, per 32x32 output tile of one channel plane, the five
+// blurred moments from a 42x42 staged input, the SSIM map, and the three
 // partial derivatives of SSIM with respect to the blurred moments m1 =
 // K*I1, m11 = K*I1^2, m12 = K*(I1 I2); it also writes per-block sums of SSIM
 // and |I1 - I2|.  Kernel 2 blurs those partials again (the filter is its own
@@ -21,9 +21,10 @@
 namespace mvgs {
 namespace {
 
-// 32 x 16 outputs per block of 256 threads (two rows per thread): the staged
-// halo is 2.1x the outputs instead of 2.6x with 16 x 16
-constexpr int TSX = 32, TSY = 16;
+// 32 x 32 outputs per block of 256 threads (four rows per thread): the staged
+// halo is 1.7x the outputs instead of 2.6x with 16 x 16
+constexpr int TSX = 32, TSY = 32;
+constexpr int ROWS = TSY / 8;  // output rows per thread
 constexpr int RADIUS = 5;            // 11 taps
 constexpr int TAPS = 2 * RADIUS + 1;
 constexpr int HSX = TSX + 2 * RADIUS, HSY = TSY + 2 * RADIUS;  // staged 42 x 26
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(256) dssim_forward_kernel(Views vw, const floa
     float ssim = 0.f, l1 = 0.f;
     const int c = threadIdx.x % TSX;
 #pragma unroll
-    for (int q = 0; q < 2; q++) {
+    for (int q = 0; q < ROWS; q++) {
         const int r = threadIdx.x / TSX + 8 * q;
         float m1 = 0.f, m2 = 0.f, m11 = 0.f, m22 = 0.f, m12 = 0.f;
 #pragma unroll
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(256) dssim_backward_kernel(Views vw, const flo
     const int c = threadIdx.x % TSX;
     const float inv_n = 1.f / (3.f * (float)p.H * (float)p.W);
 #pragma unroll
-    for (int q = 0; q < 2; q++) {
+    for (int q = 0; q < ROWS; q++) {
         const int r = threadIdx.x / TSX + 8 * q;
         const int x = p.x0 + c, y = p.y0 + r;
         if (x >= p.W || y >= p.H) continue;
