@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--tile", default="auto", help="WxH, or auto (timed choice before the measured steps)")
     ap.add_argument("--ppt", type=int, default=0, help="blend pixels per thread (0 = automatic)")
+    ap.add_argument("--smem-batch", type=int, default=0, help="Gaussians per shared-memory batch (0 = automatic)")
     ap.add_argument("--no-loop", action="store_true", help="skip the per-view launch loop")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) measurement")
@@ -148,11 +149,12 @@ def run_ours(args, rank, world):
     tuning = None
     if args.tile == "auto":
         from paper_2506_12727_gb300.autotune import autotune
-        tile, ppt, tuning = autotune(sc, cams, params)
+        tile, ppt, tuning, wb = autotune(sc, cams, params)
         args.ppt = ppt
+        args.smem_batch = wb
         args.tile = f"{tile[0]}x{tile[1]}"
     tile = tuple(int(x) for x in args.tile.split("x"))
-    rz = mvgs.Rasterizer(cams, tile=tile, pixels_per_thread=args.ppt)
+    rz = mvgs.Rasterizer(cams, tile=tile, pixels_per_thread=args.ppt, smem_batch=args.smem_batch)
     grads = {k: torch.empty_like(v) for k, v in params.items()}
     dssim_ws = torch.empty(mvgs.dssim_workspace_size(hw), dtype=torch.uint8, device=dev)
     loss = torch.empty(V, device=dev)
@@ -256,7 +258,7 @@ def run_ours(args, rank, world):
 
     graph = None
     if not args.no_graph:
-        rzg = mvgs.Rasterizer(cams, tile=tile, pixels_per_thread=args.ppt, capturable=True, headroom=1.02)
+        rzg = mvgs.Rasterizer(cams, tile=tile, pixels_per_thread=args.ppt, smem_batch=args.smem_batch, capturable=True, headroom=1.02)
         rzg.reserve(n, needed[0], needed[1])
         g_b, fits_b = graphed([rzg], [tgt], [hw], [loss], [dimg], [dssim_ws], [rzg.cap.records])
         ms_graph, _ = timed(lambda: g_b.replay(), args.steps, args.warmup)
@@ -272,7 +274,7 @@ def run_ours(args, rank, world):
             cv = cams.subset([v])
             hv = hw[v:v + 1]
             off = synth.view_offsets(cams)
-            singles.append((mvgs.Rasterizer(cv, tile=tile, pixels_per_thread=args.ppt),
+            singles.append((mvgs.Rasterizer(cv, tile=tile, pixels_per_thread=args.ppt, smem_batch=args.smem_batch),
                             tgt[off[v]:off[v + 1]].contiguous(), hv,
                             torch.empty(1, device=dev), torch.empty(int(off[v + 1] - off[v]), device=dev),
                             torch.empty(mvgs.dssim_workspace_size(hv), dtype=torch.uint8, device=dev)))
@@ -294,7 +296,7 @@ def run_ours(args, rank, world):
             # the loop captured in one CUDA graph as well (V capturable calls)
             rzs = []
             for v, (rv, tv, hv, lv, dv, wv) in enumerate(singles):
-                rg = mvgs.Rasterizer(cams.subset([v]), tile=tile, pixels_per_thread=args.ppt, capturable=True,
+                rg = mvgs.Rasterizer(cams.subset([v]), tile=tile, pixels_per_thread=args.ppt, smem_batch=args.smem_batch, capturable=True,
                                      headroom=1.02)
                 rv.forward(sc)
                 rg.reserve(n, int(rv.needed.records), int(rv.needed.keys))
@@ -433,7 +435,8 @@ def run_ours(args, rank, world):
         "config": {"workload": args.workload, "gaussians": n, "sh_degree": scene.sh_degree, "views": V,
                    "resolutions": sorted({f"{w}x{h}" for w, h in zip(cams.width, cams.height)}),
                    "loss": "0.8 L1 + 0.2 D-SSIM (11x11, sigma 1.5)", "adc": True, "tile": args.tile,
-                   "pixels_per_thread": args.ppt or "auto", "autotune_ms": tuning,
+                   "pixels_per_thread": args.ppt or "auto", "smem_batch": args.smem_batch or "auto",
+                   "autotune_ms": tuning,
                    "records": needed[0], "keys": needed[1],
                    "l2": "512 MB buffer written between timed steps (L2 is 129 MB); per-step working set > 1 GB",
                    "parallelism": (f"dp{world}: a batch of {V} views per rank, gradient and ADC all-reduce"

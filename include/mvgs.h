@@ -107,6 +107,11 @@ typedef struct mvgs_config {
                                    pixels_per_thread rows: 0 = automatic, else
                                    1, 2, 4 or 8 with the strip height dividing
                                    tile_h.  Results do not depend on it. */
+    int32_t smem_batch;         /* Gaussians a warp stages in shared memory per
+                                   batch: 0 = automatic (128), else 64, 128 or
+                                   192 (used with 4 pixels per lane; other
+                                   pixel counts use 128).  Results do not
+                                   depend on it. */
 } mvgs_config;
 
 /* cfg->flags bit for the sampled calls: blend whole strips and leave the

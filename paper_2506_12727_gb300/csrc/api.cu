@@ -143,6 +143,8 @@ mvgs_status check_config(const mvgs_config* cfg) {
     if (!side_ok) return fail(MVGS_EINVAL, "unsupported tile %dx%d (width 8, 16 or 32; height 8 to 64)", tw, th);
     if (cfg->flags & ~(uint32_t)(MVGS_FLAG_MASKED_PARTIAL | MVGS_FLAG_DEPTH | MVGS_FLAG_CAPTURABLE))
         return fail(MVGS_EINVAL, "unknown flags 0x%x", cfg->flags);
+    if (!(cfg->smem_batch == 0 || cfg->smem_batch == 64 || cfg->smem_batch == 128 || cfg->smem_batch == 192))
+        return fail(MVGS_EINVAL, "smem_batch must be 0, 64, 128 or 192");
     const int ppt = cfg->pixels_per_thread;
     if (ppt != 0) {
         // a warp covers tile_w columns and (32 / tile_w) * ppt rows of a tile
@@ -567,6 +569,7 @@ static mvgs_status render_impl(const mvgs_scene* scene, const mvgs_camera* cams,
     ba.tw = tw;
     ba.th = th;
     ba.ppt = blend_pixels_per_thread(tw, th, cfg->pixels_per_thread);
+    ba.wbatch = cfg->smem_batch ? cfg->smem_batch : 128;
     ba.strip_h = (32 / tw) * ba.ppt;
     ba.strips = th / ba.strip_h;
     ba.tiles = P.tiles;
@@ -626,6 +629,7 @@ static mvgs_status backward_impl(const mvgs_scene* scene, const mvgs_camera* cam
     ba.tw = cfg->tile_w;
     ba.th = cfg->tile_h;
     ba.ppt = blend_pixels_per_thread(ba.tw, ba.th, cfg->pixels_per_thread);
+    ba.wbatch = cfg->smem_batch ? cfg->smem_batch : 128;
     ba.strip_h = (32 / ba.tw) * ba.ppt;
     ba.strips = ba.th / ba.strip_h;
     ba.tiles = P.tiles;

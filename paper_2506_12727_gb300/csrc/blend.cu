@@ -35,7 +35,7 @@ namespace mvgs {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int WBATCH = 128;         // Gaussians per warp batch in shared memory
+constexpr int WBATCH_DEFAULT = 128;  // Gaussians per warp batch in shared memory (64 and 192 with 4 px/lane)
 constexpr int WARPS_PER_BLOCK = 4;
 
 // One warp's work item: PPT pixels per lane of one (view, tile) pair -- a
@@ -157,7 +157,7 @@ __device__ __forceinline__ bool next_work(const BlendArgs& a, int* counter, int 
     else return next_strip<PPT>(a, counter, lane, w);
 }
 
-template <int PPT, bool SAMPLED>
+template <int PPT, bool SAMPLED, int WBATCH>
 __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(BlendArgs a, int* __restrict__ counter,
                                                                              float* __restrict__ img,
                                                                              float* __restrict__ final_T,
@@ -291,7 +291,7 @@ __device__ __forceinline__ float warp_reduce_scatter16(float (&g)[16], int lane)
     return g[0] + __shfl_xor_sync(kFull, g[0], 1);
 }
 
-template <int PPT, bool SAMPLED>
+template <int PPT, bool SAMPLED, int WBATCH>
 __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(BlendArgs a, int* __restrict__ counter,
                                                                               const float* __restrict__ dimg,
                                                                               const float* __restrict__ final_T,
@@ -469,15 +469,19 @@ void launch_blend_forward(const BlendArgs& a, int* counter, float* img, float* f
     // sampled mode: the number of runs is only known on the device; launch a
     // full persistent grid
     const long long items = sampled ? (1LL << 40) : a.tiles * a.strips;
-#define MVGS_BF(P, S)                                                                                            \
-    blend_forward_kernel<P, S><<<grid_for(blend_forward_kernel<P, S>, items), 32 * WARPS_PER_BLOCK, 0, s>>>(    \
+#define MVGS_BF(P, S, B)                                                                                         \
+    blend_forward_kernel<P, S, B><<<grid_for(blend_forward_kernel<P, S, B>, items), 32 * WARPS_PER_BLOCK, 0, s>>>( \
         a, counter, img, final_T, n_contrib, pixel_stats)
-#define MVGS_BF2(P) if (sampled) MVGS_BF(P, true); else MVGS_BF(P, false)
+#define MVGS_BF2(P, B) if (sampled) MVGS_BF(P, true, B); else MVGS_BF(P, false, B)
     switch (a.ppt) {
-        case 1: MVGS_BF2(1); break;
-        case 2: MVGS_BF2(2); break;
-        case 8: MVGS_BF2(8); break;
-        default: MVGS_BF2(4); break;
+        case 1: MVGS_BF2(1, WBATCH_DEFAULT); break;
+        case 2: MVGS_BF2(2, WBATCH_DEFAULT); break;
+        case 8: MVGS_BF2(8, WBATCH_DEFAULT); break;
+        default:
+            if (a.wbatch == 64) MVGS_BF2(4, 64);
+            else if (a.wbatch == 192) MVGS_BF2(4, 192);
+            else MVGS_BF2(4, WBATCH_DEFAULT);
+            break;
     }
 #undef MVGS_BF2
 #undef MVGS_BF
@@ -490,15 +494,19 @@ void launch_blend_backward(const BlendArgs& a, int* counter, const float* dimg, 
     cudaMemsetAsync(counter, 0, sizeof(int), s);
     const bool sampled = a.s_off != nullptr;
     const long long items = sampled ? (1LL << 40) : a.tiles * a.strips;
-#define MVGS_BB(P, S)                                                                                            \
-    blend_backward_kernel<P, S><<<grid_for(blend_backward_kernel<P, S>, items), 32 * WARPS_PER_BLOCK, 0, s>>>(  \
-        a, counter, dimg, final_T, n_contrib, rec_grad, rec_conic)
-#define MVGS_BB2(P) if (sampled) MVGS_BB(P, true); else MVGS_BB(P, false)
+#define MVGS_BB(P, S, B)                                                                                         \
+    blend_backward_kernel<P, S, B><<<grid_for(blend_backward_kernel<P, S, B>, items), 32 * WARPS_PER_BLOCK, 0,   \
+                                     s>>>(a, counter, dimg, final_T, n_contrib, rec_grad, rec_conic)
+#define MVGS_BB2(P, B) if (sampled) MVGS_BB(P, true, B); else MVGS_BB(P, false, B)
     switch (a.ppt) {
-        case 1: MVGS_BB2(1); break;
-        case 2: MVGS_BB2(2); break;
-        case 8: MVGS_BB2(8); break;
-        default: MVGS_BB2(4); break;
+        case 1: MVGS_BB2(1, WBATCH_DEFAULT); break;
+        case 2: MVGS_BB2(2, WBATCH_DEFAULT); break;
+        case 8: MVGS_BB2(8, WBATCH_DEFAULT); break;
+        default:
+            if (a.wbatch == 64) MVGS_BB2(4, 64);
+            else if (a.wbatch == 192) MVGS_BB2(4, 192);
+            else MVGS_BB2(4, WBATCH_DEFAULT);
+            break;
     }
 #undef MVGS_BB2
 #undef MVGS_BB

@@ -110,6 +110,7 @@ struct BlendArgs {
     int V;
     int tw, th;
     int ppt;                 // pixels per lane (resolved, 1..8)
+    int wbatch;              // Gaussians per warp batch in shared memory (64, 128 or 192; 128 unless ppt 4)
     int strip_h;             // rows of a warp's strip: (32 / tw) * ppt
     int strips;              // strips per tile: th / strip_h
     long long tiles;

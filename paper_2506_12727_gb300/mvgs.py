@@ -48,7 +48,7 @@ class Scene(ctypes.Structure):
 
 class Config(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("bg", ctypes.c_float * 3),
-                ("flags", ctypes.c_uint32), ("pixels_per_thread", ctypes.c_int32)]
+                ("flags", ctypes.c_uint32), ("pixels_per_thread", ctypes.c_int32), ("smem_batch", ctypes.c_int32)]
 
 
 class Samples(ctypes.Structure):
@@ -190,12 +190,13 @@ def make_cameras(cams) -> ctypes.Array:
     return arr
 
 
-def make_config(tile=(16, 16), bg=(0.0, 0.0, 0.0), pixels_per_thread=0) -> Config:
+def make_config(tile=(16, 16), bg=(0.0, 0.0, 0.0), pixels_per_thread=0, smem_batch=0) -> Config:
     cfg = Config()
     cfg.tile_w, cfg.tile_h = int(tile[0]), int(tile[1])
     cfg.bg[:] = [float(b) for b in bg]
     cfg.flags = 0
     cfg.pixels_per_thread = int(pixels_per_thread)
+    cfg.smem_batch = int(smem_batch)
     return cfg
 
 
@@ -421,14 +422,14 @@ class Rasterizer:
     records or keys than the current capacity."""
 
     def __init__(self, cams, tile=(16, 16), bg=(0.0, 0.0, 0.0), device="cuda", headroom=1.15, pixels_per_thread=0,
-                 max_bytes=None, capturable=False):
+                 max_bytes=None, capturable=False, smem_batch=0):
         self.max_bytes = max_bytes  # cap on state + workspace bytes (None: unlimited)
         # capturable: no count read-backs (CUDA-graph capture); call reserve()
         # first and check counts() after a step
         self.capturable = capturable
         self.cams_np = cams
         self.cams_c = make_cameras(cams)
-        self.cfg = make_config(tile, bg, pixels_per_thread)
+        self.cfg = make_config(tile, bg, pixels_per_thread, smem_batch)
         self.device = device
         self.headroom = headroom
         self.cap = Capacity(0, 0)

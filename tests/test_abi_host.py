@@ -42,7 +42,7 @@ def test_exports_every_declared_symbol(lib):
 
 def test_struct_sizes_match_header(lib):
     assert ctypes.sizeof(lib.Camera) == 88
-    assert ctypes.sizeof(lib.Config) == 28
+    assert ctypes.sizeof(lib.Config) == 32
     assert ctypes.sizeof(lib.Scene) == 56
 
 
