@@ -305,3 +305,28 @@ def test_sort_bitexact_with_exact_depth_ties_and_many_tiles(cuda_lib, tile, nvie
     gdense = D["raw"]["v"][gsorted].astype(np.int64) * scene.n + D["raw"]["g"][gsorted]
     np.testing.assert_array_equal(gdense, recs)
     _assert_same_ranges(D["raw"]["ranges"], ranges)
+
+
+def test_results_do_not_depend_on_the_batch_size(cuda_lib):
+    # the shared-memory batch only changes how many records a warp stages at a
+    # time: images must agree bit for bit, gradients up to atomic order
+    scene, cams = CASES["multiview_sh3_ragged"]
+    params = scene_to_device(scene)
+    sc = cuda_lib.make_scene(params, scene.sh_degree)
+    dimg = None
+    imgs, grads = [], []
+    for wb in (64, 128, 192):
+        rz = cuda_lib.Rasterizer(cams, tile=(16, 32), smem_batch=wb)
+        img = rz.forward(sc).clone()
+        if dimg is None:
+            dimg = torch.randn(img.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(9))
+        gg = grads_like(params)
+        rz.backward(sc, dimg, gg)
+        torch.cuda.synchronize()
+        imgs.append(img)
+        grads.append({k: v.cpu().numpy() for k, v in gg.items()})
+    for im in imgs[1:]:
+        assert torch.equal(im, imgs[0])
+    for g in grads[1:]:
+        for k in PARAMS:
+            assert_close_frac(g[k], grads[0][k], 1e-3, 1e-6 * np.abs(grads[0][k]).max(), k)
