@@ -35,6 +35,7 @@ namespace mvgs {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+
 constexpr int WBATCH_DEFAULT = 128;  // Gaussians per warp batch in shared memory (64 and 192 with 4 px/lane)
 constexpr int WARPS_PER_BLOCK = 4;
 
@@ -157,7 +158,7 @@ __device__ __forceinline__ bool next_work(const BlendArgs& a, int* counter, int 
     else return next_strip<PPT>(a, counter, lane, w);
 }
 
-template <int PPT, bool SAMPLED, int WBATCH>
+template <int PPT, bool SAMPLED, int WBATCH, bool DEPTH>
 __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(BlendArgs a, int* __restrict__ counter,
                                                                              float* __restrict__ img,
                                                                              float* __restrict__ final_T,
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(Ble
     __shared__ float4 s_co[WARPS_PER_BLOCK][WBATCH];
     __shared__ float4 s_rgb[WARPS_PER_BLOCK][WBATCH];
     __shared__ uint32_t s_pos[WARPS_PER_BLOCK][WBATCH];
-    __shared__ float s_dep[WARPS_PER_BLOCK][WBATCH];
+    __shared__ float s_dep[WARPS_PER_BLOCK][DEPTH ? WBATCH : 1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     float2* wxy = s_xy[w];
@@ -175,7 +176,6 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(Ble
     float4* wrgb = s_rgb[w];
     uint32_t* wpos = s_pos[w];
     float* wdep = s_dep[w];
-    const bool want_depth = a.depth_out != nullptr;
     constexpr uint32_t ALL = (1u << PPT) - 1u;
     const long long total = SAMPLED ? min(a.chunk_off[a.tiles], a.chunk_cap) : 0;
     Work<PPT> st;
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(Ble
                     wco[slot] = co;
                     wrgb[slot] = cr;
                     wpos[slot] = (uint32_t)(idx - start);
-                    if (want_depth) wdep[slot] = a.rec_depth[r];
+                    if (DEPTH) wdep[slot] = a.rec_depth[r];
                 }
                 n += __popc(bal);
             }
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(Ble
                 if (!SAMPLED && fabsf(dx0) > cr.w) continue;  // outside the support for the whole column
                 const float4 co = wco[j];
                 const uint32_t pos = wpos[j];
-                const float dep = want_depth ? wdep[j] : 0.f;
+                const float dep = DEPTH ? wdep[j] : 0.f;
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
                     if ((done >> k) & 1u) continue;
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(Ble
                     C0[k] = __fmaf_rn(cr.x, wgt, C0[k]);
                     C1[k] = __fmaf_rn(cr.y, wgt, C1[k]);
                     C2[k] = __fmaf_rn(cr.z, wgt, C2[k]);
-                    D[k] = __fmaf_rn(dep, wgt, D[k]);
+                    if (DEPTH) D[k] = __fmaf_rn(dep, wgt, D[k]);
                     T[k] = Tn;
                     last[k] = pos + 1;
                     nblend[k]++;
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(Ble
                 final_T[cam.pix_base + p] = T[k];
                 n_contrib[cam.pix_base + p] = last[k];
                 pixel_stats[cam.pix_base + p] = make_uint2(stop[k], nblend[k]);
-                if (want_depth) a.depth_out[cam.pix_base + p] = D[k];
+                if (DEPTH) a.depth_out[cam.pix_base + p] = D[k];
             }
         }
     }
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(Bl
                         float alpha, G, ax, ay;
                         if (!pair_eval(dx, dy, co, cr.w, alpha, G, ax, ay)) continue;
                         any = true;
-                        const float inv = __frcp_rn(1.f - alpha);
+                        const float inv = rcp_approx(1.f - alpha);
                         T[k] *= inv;  // transmittance in front of this Gaussian
                         const float wgt = alpha * T[k];
                         g[6] += d0[k] * wgt;
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(Bl
                             g[3] += 2.f * h * dx * dy;
                             g[4] += h * dy * dy;
                             g[5] += dLda * G;
-                            g[9] += sqrtf(gx * gx + gy * gy);
+                            g[9] += sqrt_approx(gx * gx + gy * gy);
                         }
                     }
                 }
@@ -468,11 +468,25 @@ void launch_blend_forward(const BlendArgs& a, int* counter, float* img, float* f
     const bool sampled = a.s_off != nullptr;
     // sampled mode: the number of runs is only known on the device; launch a
     // full persistent grid
+    const bool depth = a.depth_out != nullptr;
     const long long items = sampled ? (1LL << 40) : a.tiles * a.strips;
-#define MVGS_BF(P, S, B)                                                                                         \
-    blend_forward_kernel<P, S, B><<<grid_for(blend_forward_kernel<P, S, B>, items), 32 * WARPS_PER_BLOCK, 0, s>>>( \
-        a, counter, img, final_T, n_contrib, pixel_stats)
-#define MVGS_BF2(P, B) if (sampled) MVGS_BF(P, true, B); else MVGS_BF(P, false, B)
+#define MVGS_BF1(P, S, B, D)                                                                                 \
+    blend_forward_kernel<P, S, B, D><<<grid_for(blend_forward_kernel<P, S, B, D>, items), 32 * WARPS_PER_BLOCK, 0, \
+                                       s>>>(a, counter, img, final_T, n_contrib, pixel_stats)
+#define MVGS_BF(P, S, B)              \
+    do {                              \
+        if (depth)                    \
+            MVGS_BF1(P, S, B, true);  \
+        else                          \
+            MVGS_BF1(P, S, B, false); \
+    } while (0)
+#define MVGS_BF2(P, B)              \
+    do {                            \
+        if (sampled)                \
+            MVGS_BF(P, true, B);    \
+        else                        \
+            MVGS_BF(P, false, B);   \
+    } while (0)
     switch (a.ppt) {
         case 1: MVGS_BF2(1, WBATCH_DEFAULT); break;
         case 2: MVGS_BF2(2, WBATCH_DEFAULT); break;
@@ -485,6 +499,7 @@ void launch_blend_forward(const BlendArgs& a, int* counter, float* img, float* f
     }
 #undef MVGS_BF2
 #undef MVGS_BF
+#undef MVGS_BF1
     note_launches(1);
 }
 

@@ -60,6 +60,25 @@ struct CamChunk {
 constexpr int kGradStride = 12;
 
 // Global tile ids index the view-major list of (view, tile) pairs.
+// Single-instruction approximations (PTX rcp.approx / sqrt.approx, about
+// 1 ulp; flush-to-zero) for per-pair arithmetic, where the correctly rounded
+// forms (__frcp_rn, IEEE sqrtf and division) are instruction sequences with a
+// slow path.  The blend backward recovers T by a reciprocal and sums
+// |dL/dmean2d| with a square root on every blended pair: the exact forms cost
+// a fifth of that kernel, and the approximations are far inside the gradient
+// tolerance of 1e-3 relative.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ int find_view(const DevCam* cams, int V, long long gt) {
     int lo = 0, hi = V - 1;
     while (lo < hi) {
@@ -115,7 +134,9 @@ __device__ __forceinline__ bool pair_eval(float dx, float dy, float4 co, float r
 // rectangle that is 0 if it holds the mean, else on an edge, where q is a
 // 1D quadratic minimised in closed form.  alpha >= 1/255 needs
 // q <= 2 ln(255 o); the margin keeps the test a superset of what any pixel's
-// float32 evaluation lets through.
+// float32 evaluation lets through.  The edge minimisers use approximate
+// reciprocals: a point off the minimiser by a relative 1e-7 raises q by a
+// second-order amount, far inside the margin.
 __device__ __forceinline__ bool rect_reaches(float x0, float x1, float y0, float y1, float4 co, float radius) {
     if (x0 > radius || x1 < -radius || y0 > radius || y1 < -radius) return false;
     const float lvl = 2.f * __logf(255.f * co.w);
@@ -124,7 +145,7 @@ __device__ __forceinline__ bool rect_reaches(float x0, float x1, float y0, float
     const float A = co.x, B = co.y, C = co.z;
     auto q = [&](float x, float y) { return A * x * x + 2.f * B * x * y + C * y * y; };
     // edges x = x0, x = x1: minimise over y in [y0, y1]
-    const float iC = 1.f / C, iA = 1.f / A;
+    const float iC = rcp_approx(C), iA = rcp_approx(A);
     float best = 3.4e38f;
     {
         const float ya = fminf(fmaxf(-B * x0 * iC, y0), y1);

@@ -122,13 +122,15 @@ __global__ void __launch_bounds__(256) dssim_forward_kernel(Views vw, const floa
             const float t11 = m11 - m1 * m1, t22 = m22 - m2 * m2, t12 = m12 - m1 * m2;
             const float a1 = 2.f * m1 * m2 + kC1, a2 = 2.f * t12 + kC2;
             const float b1 = m1 * m1 + m2 * m2 + kC1, b2 = t11 + t22 + kC2;
-            const float ia1 = 1.f / a1, ia2 = 1.f / a2, ib1 = 1.f / b1, ib2 = 1.f / b2;
-            const float sv = a1 * a2 * ib1 * ib2;
+            // only the denominators b1, b2 (>= C1, C2 > 0) are inverted: S / a_k
+            // is written as a product, so a vanishing a2 = 2 cov + C2 is harmless
+            const float ib1 = rcp_approx(b1), ib2 = rcp_approx(b2), q = ib1 * ib2;
+            const float sv = a1 * a2 * q;
             ssim += sv;
             const long long o = p.plane + (long long)y * p.W + x;
-            dm1[o] = 2.f * sv * (m2 * ia1 - m2 * ia2 - m1 * ib1 + m1 * ib2);
+            dm1[o] = 2.f * (m2 * (a2 - a1) * q + m1 * sv * (ib2 - ib1));
             dm11[o] = -sv * ib2;
-            dm12[o] = 2.f * sv * ia2;
+            dm12[o] = 2.f * a1 * q;
             l1 += fabsf(s1[r + RADIUS][c + RADIUS] - s2[r + RADIUS][c + RADIUS]);
         }
     }
