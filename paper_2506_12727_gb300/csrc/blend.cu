@@ -18,12 +18,15 @@
 //
 // Forward per pixel (front to back): alpha = min(0.99, o G), skip alpha <
 // 1/255, stop before T (1 - alpha) < 1e-4, C += c alpha T, T *= 1 - alpha;
-// output C + T bg.
+// output C + T bg.  G is evaluated in base 2 from the staged coefficients
+// and the column terms of the lane's pixel column (pair_eval).
 //
 // Backward per pixel (back to front from the last contributor), with T
-// recovered by division:  dC/dc_i = alpha_i T_i,  dC/dalpha_i = c_i T_i -
-// S_i / (1 - alpha_i), S_i the colour blended behind i plus T_final bg.  The
-// gradients of one Gaussian are summed over the lane's pixels, then over the
+// recovered by an (approximate) reciprocal:  dC/dc_i = alpha_i T_i,
+// dC/dalpha_i = c_i T_i - S_i / (1 - alpha_i), S_i the colour blended behind
+// i plus T_final bg.  The gradients of one Gaussian are summed over the
+// lane's pixels (in a strip, as sums of dL/dpower times 1, dy, dy^2 for the
+// lane's one column), then over the
 // warp by a reduce-scatter (16 shuffles for 10 values), and each lane pair
 // adds one value with one atomic.
 #include <mutex>
@@ -158,8 +161,15 @@ __device__ __forceinline__ bool next_work(const BlendArgs& a, int* counter, int 
     else return next_strip<PPT>(a, counter, lane, w);
 }
 
+// Resident blocks per SM the forward is compiled for: six (80 registers) for
+// strips of 4 pixels per lane without the depth output, where ptxas keeps
+// the state in registers (8 bytes spilled) and the extra warps hide more
+// latency than the registers given up cost; no bound elsewhere (more state
+// there, and a bound spills it).
+constexpr int fwd_min_blocks(int ppt, bool sampled, bool depth) { return ppt == 4 && !sampled && !depth ? 6 : 1; }
+
 template <int PPT, bool SAMPLED, int WBATCH, bool DEPTH>
-__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(BlendArgs a, int* __restrict__ counter,
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, fwd_min_blocks(PPT, SAMPLED, DEPTH)) blend_forward_kernel(BlendArgs a, int* __restrict__ counter,
                                                                              float* __restrict__ img,
                                                                              float* __restrict__ final_T,
                                                                              uint32_t* __restrict__ n_contrib,
@@ -216,7 +226,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(Ble
                 if (hit) {
                     const int slot = n + __popc(bal & lt);
                     wxy[slot] = m;
-                    wco[slot] = co;
+                    wco[slot] = exp2_coeffs(co);
                     wrgb[slot] = cr;
                     wpos[slot] = (uint32_t)(idx - start);
                     if (DEPTH) wdep[slot] = a.rec_depth[r];
@@ -229,15 +239,17 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_forward_kernel(Ble
                 const float4 cr = wrgb[j];
                 const float dx0 = st.fx[0] - m.x;
                 if (!SAMPLED && fabsf(dx0) > cr.w) continue;  // outside the support for the whole column
-                const float4 co = wco[j];
+                const float4 q = wco[j];
                 const uint32_t pos = wpos[j];
                 const float dep = DEPTH ? wdep[j] : 0.f;
+                const ColTerms ct0 = col_terms(dx0, q);
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
                     if ((done >> k) & 1u) continue;
                     const float dx = SAMPLED ? st.fx[k] - m.x : dx0;
-                    float alpha, G, ax, ay;
-                    if (!pair_eval(dx, st.fy[k] - m.y, co, cr.w, alpha, G, ax, ay)) continue;
+                    const ColTerms ct = SAMPLED ? col_terms(dx, q) : ct0;
+                    float alpha, G;
+                    if (!pair_eval(dx, st.fy[k] - m.y, ct, q, cr.w, alpha, G)) continue;
                     const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
                     if (Tn < kTMin) {
                         done |= 1u << k;
@@ -364,7 +376,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(Bl
                     const int slot = n + __popc(bal & lt);
                     wrid[slot] = r;
                     wxy[slot] = m;
-                    wco[slot] = co;
+                    wco[slot] = exp2_coeffs(co);
                     wrgb[slot] = cr;
                     wpos[slot] = (uint32_t)pos;
                 }
@@ -381,14 +393,22 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(Bl
                 const float4 cr = wrgb[j];
                 const float dx0 = st.fx[0] - m.x;
                 if (pos < mylast && (SAMPLED || fabsf(dx0) <= cr.w)) {
-                    const float4 co = wco[j];
+                    const float4 q = wco[j];
+                    const float3 cn = conic_of(q);  // (A, B, C)
+                    const ColTerms ct0 = col_terms(dx0, q);
+                    const float adx0 = cn.x * dx0, bdx0 = cn.y * dx0;
+                    // strips (one column per lane): sums over the lane's pixels of
+                    // dL/dpower times 1, dy and dy^2, turned into the mean and conic
+                    // gradients once per Gaussian below
+                    float P0 = 0.f, P1 = 0.f, P2 = 0.f;
 #pragma unroll
                     for (int k = 0; k < PPT; k++) {
                         if (pos >= last[k]) continue;
                         const float dx = SAMPLED ? st.fx[k] - m.x : dx0;
                         const float dy = st.fy[k] - m.y;
-                        float alpha, G, ax, ay;
-                        if (!pair_eval(dx, dy, co, cr.w, alpha, G, ax, ay)) continue;
+                        const ColTerms ct = SAMPLED ? col_terms(dx, q) : ct0;
+                        float alpha, G;
+                        if (!pair_eval(dx, dy, ct, q, cr.w, alpha, G)) continue;
                         any = true;
                         const float inv = rcp_approx(1.f - alpha);
                         T[k] *= inv;  // transmittance in front of this Gaussian
@@ -399,19 +419,35 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(Bl
                         const float dc = d0[k] * cr.x + d1[k] * cr.y + d2[k] * cr.z;
                         const float dLda = T[k] * dc - U[k] * inv;
                         U[k] += dc * wgt;
-                        if (co.w * G < kAlphaMax) {  // below the clamp alpha = o G
+                        if (alpha < kAlphaMax) {  // below the clamp alpha = o G
                             const float dLdp = dLda * alpha;  // dL/d power = dL/dalpha o G
-                            const float gx = dLdp * ax;       // d power / d mean2d = (ax, ay)
-                            const float gy = dLdp * ay;
-                            const float h = -0.5f * dLdp;
-                            g[0] += gx;
-                            g[1] += gy;
-                            g[2] += h * dx * dx;
-                            g[3] += 2.f * h * dx * dy;
-                            g[4] += h * dy * dy;
+                            // d power / d mean2d = (ax, ay) = (A dx + B dy, B dx + C dy)
+                            const float ax = fmaf(cn.y, dy, SAMPLED ? cn.x * dx : adx0);
+                            const float ay = fmaf(cn.z, dy, SAMPLED ? cn.y * dx : bdx0);
+                            if (SAMPLED) {
+                                const float h = -0.5f * dLdp;
+                                g[0] += dLdp * ax;
+                                g[1] += dLdp * ay;
+                                g[2] += h * dx * dx;
+                                g[3] += 2.f * h * dx * dy;
+                                g[4] += h * dy * dy;
+                            } else {
+                                const float e = dLdp * dy;
+                                P0 += dLdp;
+                                P1 += e;
+                                P2 = fmaf(e, dy, P2);
+                            }
                             g[5] += dLda * G;
-                            g[9] += sqrt_approx(gx * gx + gy * gy);
+                            g[9] += fabsf(dLdp) * sqrt_approx(ax * ax + ay * ay);
                         }
+                    }
+                    if (!SAMPLED) {
+                        // sum_k dL/dpower_k (ax_k, ay_k) and -1/2 sum_k dL/dpower_k (dx^2, 2 dx dy_k, dy_k^2)
+                        g[0] = fmaf(adx0, P0, cn.y * P1);
+                        g[1] = fmaf(bdx0, P0, cn.z * P1);
+                        g[2] = -0.5f * dx0 * dx0 * P0;
+                        g[3] = -dx0 * P1;
+                        g[4] = -0.5f * P2;
                     }
                 }
                 if (__ballot_sync(kFull, any) == 0u) continue;

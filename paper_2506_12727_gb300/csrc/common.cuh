@@ -105,26 +105,58 @@ __device__ __forceinline__ int sample_slot(unsigned long long seed, int x, int y
     return (int)(((h >> 32) * (unsigned long long)group) >> 32);
 }
 
+// 2^x for the blend exponent (PTX ex2.approx, relative error near 2^-22;
+// results below 2^-126 flush to zero, far under the 1/255 skip threshold).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// The blend exponent in base 2.  With conic (A, B, C), d = pixel centre
+// minus projected mean and L = log2 e,
+//   power L = -(A dx^2 + 2 B dx dy + C dy^2) L / 2 = qa dx^2 + qb dx dy + qc dy^2,
+// q = (qa, qb, qc) = (-A L / 2, -B L, -C L / 2), so G = exp(power) is one
+// ex2 of a two-FMA polynomial in dy once the column terms (qa dx^2, qb dx)
+// of the pixel's column are known.  A lane of a strip owns one column: it
+// computes the column terms once per Gaussian and reuses them for its PPT
+// pixels.
+__device__ __forceinline__ float4 exp2_coeffs(float4 co) {
+    constexpr float L = 1.4426950408889634f;
+    return make_float4(__fmul_rn(-0.5f * L, co.x), __fmul_rn(-L, co.y), __fmul_rn(-0.5f * L, co.z), co.w);
+}
+
+// Conic (A, B, C) back from the base-2 coefficients (gradients need it).
+__device__ __forceinline__ float3 conic_of(float4 q) {
+    constexpr float LN2 = 0.6931471805599453f;
+    return make_float3(-2.f * LN2 * q.x, -LN2 * q.y, -2.f * LN2 * q.z);
+}
+
+struct ColTerms {
+    float xx, x;  // qa dx^2 and qb dx
+};
+
+__device__ __forceinline__ ColTerms col_terms(float dx, float4 q) {
+    return ColTerms{__fmul_rn(__fmul_rn(q.x, dx), dx), __fmul_rn(q.y, dx)};
+}
+
 // The blend decision and opacity of one (pixel, Gaussian) pair (Eq. 1 with
-// the 3DGS clamp and skip rules and the per-pixel support rule), d = pixel
-// centre minus projected mean, conic (A, B, C) so that the exponent is
-// power = -(A dx^2 + 2 B dx dy + C dy^2) / 2 = -(dx ax + dy ay) / 2 with
-// (ax, ay) = (A dx + B dy, B dx + C dy).  Everything is evaluated
-// unconditionally; the return value says whether the Gaussian takes part at
-// this pixel, and alpha, G = exp(power) and (ax, ay) are valid when it does.
-// The forward and the backward call this same function, so both take the
-// same decision for every pair.  The products and fused multiply-adds are
-// spelled out (no contraction left to the compiler), so every kernel that
-// inlines it -- strips, sample runs, any pixels per lane -- rounds a pair the
-// same way.
-__device__ __forceinline__ bool pair_eval(float dx, float dy, float4 co, float radius, float& alpha, float& G,
-                                          float& ax, float& ay) {
-    ax = __fmaf_rn(co.y, dy, __fmul_rn(co.x, dx));
-    ay = __fmaf_rn(co.z, dy, __fmul_rn(co.y, dx));
-    const float power = __fmul_rn(-0.5f, __fmaf_rn(dy, ay, __fmul_rn(dx, ax)));
-    G = __expf(power);
-    alpha = fminf(kAlphaMax, co.w * G);
-    return fabsf(dx) <= radius && fabsf(dy) <= radius && power <= 0.f && alpha >= kAlphaMin;
+// the 3DGS clamp and skip rules and the per-pixel support rule); q holds the
+// base-2 coefficients and the opacity (q.w), ct the column terms of dx.
+// Everything is evaluated unconditionally; the return value says whether the
+// Gaussian takes part at this pixel, and alpha and G = exp(power) are valid
+// when it does.  The forward and the backward call this same function with
+// the same inputs, so both take the same decision for every pair.  The
+// products and fused multiply-adds are spelled out (no contraction left to
+// the compiler), and the column terms are the same products whether a lane
+// reuses them (strips) or computes them per pixel (sample runs), so every
+// kernel rounds a pair the same way.
+__device__ __forceinline__ bool pair_eval(float dx, float dy, ColTerms ct, float4 q, float radius, float& alpha,
+                                          float& G) {
+    const float e = __fmaf_rn(dy, __fmaf_rn(q.z, dy, ct.x), ct.xx);
+    G = ex2_approx(e);
+    alpha = fminf(kAlphaMax, __fmul_rn(q.w, G));
+    return fabsf(dx) <= radius && fabsf(dy) <= radius && e <= 0.f && alpha >= kAlphaMin;
 }
 
 // Whether a Gaussian can pass the support rule and alpha >= 1/255 at any

@@ -121,9 +121,12 @@ def test_central_differences_on_64_parameters(setup):
         g = int(rng.choice(strong))
         comp = tuple(int(rng.integers(0, s)) for s in params[kind].shape[1:])
         picks.append((kind, (g,) + comp))
-    # step per kind: the colour is linear in sh and smooth in the opacity
-    # logit, so a larger step there only lowers the rounding noise
-    steps = dict(means=2e-3, log_scales=2e-3, quats=2e-3, opacity_logits=1e-2, sh=1e-2)
+    # step per kind: the float32 rounding of the two renders enters the
+    # difference quotient as 1/h while the central-difference error is O(h^2);
+    # the colour is linear in sh and smooth in the opacity logit, and the
+    # footprint smooth in the log-scales and the rotation, so larger steps
+    # there only lower the rounding noise
+    steps = dict(means=2e-3, log_scales=5e-3, quats=5e-3, opacity_logits=1e-2, sh=1e-2)
     errs, scales, kinds, ok = [], [], [], 0
     for kind, idx in picks:
         t = params[kind]
