@@ -229,6 +229,11 @@ def run_ours(args, rank, world):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_batched = float(t.item())
     needed = (int(rz.needed.records), int(rz.needed.keys))
+    # blended (pixel, Gaussian) pairs of the step, the unit of the blend
+    # kernels' work: counted by one more forward with the per-pixel statistics
+    # (off in the timed steps), outside the timed region
+    rz.forward(sc, stats=True)
+    blended = int(rz.records()["pixel_stats"].to(torch.int64)[:, 1].sum().item())
 
     # ---- the same step captured in a CUDA graph (capturable mode) ----
     def graphed(rasterizers, tgts, hws, losses, dimgs, wss, rec_caps):
@@ -433,7 +438,7 @@ def run_ours(args, rank, world):
     ms_e2e = None if args.no_e2e else timed(e2e_step, max(3, args.steps // 2), 2)[0]
 
     # ---- roofline of the dominant kernel ----
-    roof, per_stage = roofline(stages, args, needed, rz, clk, V, rz.pixels)
+    roof, per_stage = roofline(stages, args, needed, rz, clk, V, rz.pixels, blended)
 
     out = {
         "metric": METRIC, "value": V * world / (ms_batched / 1e3), "unit": "views/s", "n_gpus": world,
@@ -533,17 +538,15 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def stage_work(rz, needed, V, pixels):
+def stage_work(rz, needed, V, pixels, blended):
     """Algorithmic work of each stage for one step: (bound, amount, unit).
     Bytes are what the stage must read and write in HBM (each array once);
     FLOPs are counted on blended pairs only (see FWD_/BWD_FLOP_PER_BLENDED)."""
-    import torch
     R, K = needed
     n = rz.n
     tiles = int(rz.layout.tiles)
     bits = max(1, int(np.ceil(np.log2(max(tiles, 2)))))
     passes = max(1, (bits + 7) // 8)
-    blended = rz.records()["pixel_stats"].to(torch.int64)[:, 1].sum().item()
     return {
         "count_visible": ("hbm", 44.0 * n + 4.0 * n + n * V, "B"),
         "scan_records": ("hbm", 12.0 * n, "B"),
@@ -569,7 +572,7 @@ def stage_work(rz, needed, V, pixels):
 DRAM_BYTES_PER_BLENDED = {"blend_forward": 22.622464e6 / 103536139, "blend_backward": 50.347776e6 / 103536139}
 
 
-def roofline(stages, args, needed, rz, clk, V, pixels):
+def roofline(stages, args, needed, rz, clk, V, pixels, blended):
     """Per-stage achieved / peak, and the dominant stage's entry."""
     if not stages:
         return None, None
@@ -579,7 +582,7 @@ def roofline(stages, args, needed, rz, clk, V, pixels):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1455.0)
     alu_peak = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-    work, blended = stage_work(rz, needed, V, pixels)
+    work, blended = stage_work(rz, needed, V, pixels, blended)
     table = {}
     for name, (ms_total, launches) in stages.items():
         if not launches or name not in work:

@@ -133,6 +133,11 @@ typedef struct mvgs_config {
  * otherwise the records and keys past it were dropped, and the caller grows
  * the buffers and runs again. */
 #define MVGS_FLAG_CAPTURABLE 4u
+/* cfg->flags bit for the forward calls: also write the per-pixel statistics
+ * (layout.off_pixel_stats: where the pixel stopped and how many Gaussians it
+ * blended).  Counting costs about 5% of the blend forward, so it is off by
+ * default and the array is then left as it was. */
+#define MVGS_FLAG_PIXEL_STATS 8u
 
 /* Capacities the caller sized `state` and `workspace` for:
  * records = visible (Gaussian, view) pairs, keys = (record, tile) pairs. */
@@ -165,7 +170,8 @@ typedef struct mvgs_layout {
     size_t off_final_T;              /* float[pixels]: transmittance after blending */
     size_t off_n_contrib;            /* uint32[pixels]: list position one past the last contributor */
     size_t off_pixel_stats;          /* uint32x2[pixels]: list entries the pixel examined before it
-                                        stopped, and the number of Gaussians it blended */
+                                        stopped, and the number of Gaussians it blended
+                                        (with MVGS_FLAG_PIXEL_STATS) */
     size_t off_pixel_depth;          /* float[pixels]: expected depth (with MVGS_FLAG_DEPTH) */
     int64_t tiles;                   /* total tiles over all views                 */
     int64_t pixels;                  /* total pixels over all views                */

@@ -141,7 +141,8 @@ mvgs_status check_config(const mvgs_config* cfg) {
     const int tw = cfg->tile_w, th = cfg->tile_h;
     const bool side_ok = (tw == 8 || tw == 16 || tw == 32) && (th == 8 || th == 16 || th == 32 || th == 64);
     if (!side_ok) return fail(MVGS_EINVAL, "unsupported tile %dx%d (width 8, 16 or 32; height 8 to 64)", tw, th);
-    if (cfg->flags & ~(uint32_t)(MVGS_FLAG_MASKED_PARTIAL | MVGS_FLAG_DEPTH | MVGS_FLAG_CAPTURABLE))
+    if (cfg->flags & ~(uint32_t)(MVGS_FLAG_MASKED_PARTIAL | MVGS_FLAG_DEPTH | MVGS_FLAG_CAPTURABLE |
+                                 MVGS_FLAG_PIXEL_STATS))
         return fail(MVGS_EINVAL, "unknown flags 0x%x", cfg->flags);
     if (!(cfg->smem_batch == 0 || cfg->smem_batch == 64 || cfg->smem_batch == 128 || cfg->smem_batch == 192))
         return fail(MVGS_EINVAL, "smem_batch must be 0, 64, 128 or 192");
@@ -586,7 +587,9 @@ static mvgs_status render_impl(const mvgs_scene* scene, const mvgs_camera* cams,
         StageTimer t(MVGS_STAGE_BLEND_FORWARD, s);
         attach_samples(ba, smp, cfg, P, workspace, P.w_chunk_off, P.w_chunk_map, P.w_chunk_tmp, P.w_mask, s);
         launch_blend_forward(ba, at<int>(workspace, P.w_counter), images, at<float>(state, L.off_final_T),
-                             at<uint32_t>(state, L.off_n_contrib), at<uint2>(state, L.off_pixel_stats), s);
+                             at<uint32_t>(state, L.off_n_contrib),
+                             (cfg->flags & MVGS_FLAG_PIXEL_STATS) ? at<uint2>(state, L.off_pixel_stats) : nullptr,
+                             s);
     }
     return cuda_check("render");
 }

@@ -27,8 +27,8 @@
 // i plus T_final bg.  The gradients of one Gaussian are summed over the
 // lane's pixels (in a strip, as sums of dL/dpower times 1, dy, dy^2 for the
 // lane's one column), then over the
-// warp by a reduce-scatter (16 shuffles for 10 values), and each lane pair
-// adds one value with one atomic.
+// warp by a reduce-scatter (12 shuffles for 10 values), and one lane per
+// value adds it with one atomic.
 #include <mutex>
 #include <unordered_map>
 
@@ -161,15 +161,18 @@ __device__ __forceinline__ bool next_work(const BlendArgs& a, int* counter, int 
     else return next_strip<PPT>(a, counter, lane, w);
 }
 
-// Resident blocks per SM the forward is compiled for: six (80 registers) for
-// strips of 4 pixels per lane without the depth output, where ptxas keeps
-// the state in registers (8 bytes spilled) and the extra warps hide more
-// latency than the registers given up cost; no bound elsewhere (more state
-// there, and a bound spills it).
-constexpr int fwd_min_blocks(int ppt, bool sampled, bool depth) { return ppt == 4 && !sampled && !depth ? 6 : 1; }
+// Resident blocks per SM the forward is compiled for: six (at most 80
+// registers) for strips of 4 pixels per lane without the depth and statistics
+// outputs, where the state fits without spilling and the extra warps hide
+// more latency than the registers given up cost; no bound elsewhere (more
+// state there, and a bound spills it).
+constexpr int fwd_min_blocks(int ppt, bool sampled, bool extra) { return ppt == 4 && !sampled && !extra ? 6 : 1; }
 
-template <int PPT, bool SAMPLED, int WBATCH, bool DEPTH>
-__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, fwd_min_blocks(PPT, SAMPLED, DEPTH)) blend_forward_kernel(BlendArgs a, int* __restrict__ counter,
+// DEPTH: also the expected depth per pixel; STATS: also the per-pixel
+// statistics (list position where the pixel stopped, Gaussians blended).
+template <int PPT, bool SAMPLED, int WBATCH, bool DEPTH, bool STATS>
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, fwd_min_blocks(PPT, SAMPLED, DEPTH || STATS))
+    blend_forward_kernel(BlendArgs a, int* __restrict__ counter,
                                                                              float* __restrict__ img,
                                                                              float* __restrict__ final_T,
                                                                              uint32_t* __restrict__ n_contrib,
@@ -253,7 +256,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, fwd_min_blocks(PPT, SAMP
                     const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
                     if (Tn < kTMin) {
                         done |= 1u << k;
-                        stop[k] = pos + 1;
+                        if (STATS) stop[k] = pos + 1;
                         continue;
                     }
                     const float wgt = __fmul_rn(alpha, T[k]);
@@ -263,7 +266,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, fwd_min_blocks(PPT, SAMP
                     if (DEPTH) D[k] = __fmaf_rn(dep, wgt, D[k]);
                     T[k] = Tn;
                     last[k] = pos + 1;
-                    nblend[k]++;
+                    if (STATS) nblend[k]++;
                 }
                 if (done == ALL) break;
             }
@@ -279,28 +282,51 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, fwd_min_blocks(PPT, SAMP
                 out[2 * HW + p] = __fmaf_rn(T[k], a.bg[2], C2[k]);
                 final_T[cam.pix_base + p] = T[k];
                 n_contrib[cam.pix_base + p] = last[k];
-                pixel_stats[cam.pix_base + p] = make_uint2(stop[k], nblend[k]);
+                if (STATS) pixel_stats[cam.pix_base + p] = make_uint2(stop[k], nblend[k]);
                 if (DEPTH) a.depth_out[cam.pix_base + p] = D[k];
             }
         }
     }
 }
 
-// Sum over the warp of 16 values per lane, scattered: afterwards lane l holds
-// the full sum of value 8 b4 + 4 b3 + 2 b2 + b1 (b_i the bits of l), in both
-// lanes of each pair (l, l ^ 1).
-__device__ __forceinline__ float warp_reduce_scatter16(float (&g)[16], int lane) {
+// Sum over the warp of 10 values per lane, scattered: 12 shuffles in five
+// halving steps (5 + 3 + 2 + 1 + 1), after which every lane holds the full sum
+// of one value, value_of_lane(lane).
+__device__ __forceinline__ int value_of_lane(int lane) {
+    const int b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1, b1 = (lane >> 1) & 1;
+    return 5 * b4 + (b3 ? 3 + b2 : (b2 ? 2 : b1));
+}
+
+__device__ __forceinline__ float warp_reduce_scatter10(const float (&g)[10], int lane) {
+    const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0, b2 = (lane & 4) != 0, b1 = (lane & 2) != 0;
+    // step 1 (lanes l, l^16): values 0-4 stay in the lower, 5-9 in the upper half
+    float a[5];
 #pragma unroll
-    for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
-        const bool up = (lane & o) != 0;
-#pragma unroll
-        for (int i = 0; i < h; i++) {
-            const float send = up ? g[i] : g[i + h];
-            const float keep = up ? g[i + h] : g[i];
-            g[i] = keep + __shfl_xor_sync(kFull, send, o);
-        }
+    for (int i = 0; i < 5; i++) {
+        const float send = b4 ? g[i] : g[i + 5];
+        const float keep = b4 ? g[i + 5] : g[i];
+        a[i] = keep + __shfl_xor_sync(kFull, send, 16);
     }
-    return g[0] + __shfl_xor_sync(kFull, g[0], 1);
+    // step 2 (l^8): a0-a2 stay in the lower, a3-a4 in the upper half
+    float b[3];
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const float send = b3 ? a[i] : a[3 + i];
+        const float keep = b3 ? a[3 + i] : a[i];
+        b[i] = keep + __shfl_xor_sync(kFull, send, 8);
+    }
+    b[2] = a[2] + __shfl_xor_sync(kFull, a[2], 8);
+    // step 3 (l^4): three values split 2 + 1, two values 1 + 1
+    const float send0 = b2 ? b[0] : (b3 ? b[1] : b[2]);
+    const float keep0 = b2 ? (b3 ? b[1] : b[2]) : b[0];
+    const float c0 = keep0 + __shfl_xor_sync(kFull, send0, 4);
+    const float c1 = b[1] + __shfl_xor_sync(kFull, b[1], 4);
+    // step 4 (l^2): the two-value lanes split 1 + 1, the others add
+    const bool two = !b3 && !b2;
+    const float send = (two && !b1) ? c1 : c0;
+    const float keep = (two && b1) ? c1 : c0;
+    const float d = keep + __shfl_xor_sync(kFull, send, 2);
+    return d + __shfl_xor_sync(kFull, d, 1);
 }
 
 template <int PPT, bool SAMPLED, int WBATCH>
@@ -322,9 +348,11 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(Bl
     float4* wrgb = s_rgb[w];
     uint32_t* wrid = s_rid[w];
     uint32_t* wpos = s_pos[w];
-    // value this lane adds after the reduce-scatter (lane pairs share one)
-    const int my_val = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-    const bool adder = (lane & 1) == 0 && my_val < 10;
+    // the value this lane holds after the reduce-scatter
+    const int my_val = value_of_lane(lane);
+    // one lane per value: value_of_lane is the same for lanes l, l^1 and, where
+    // it ignores bit 1, for l^2
+    const bool adder = (lane & 1) == 0 && ((lane & 12) == 0 || (lane & 2) == 0);
     const long long total = SAMPLED ? min(a.chunk_off[a.tiles], a.chunk_cap) : 0;
     Work<PPT> st;
     while (next_work<PPT, SAMPLED>(a, counter, lane, total, st)) {
@@ -385,9 +413,9 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(Bl
             __syncwarp();
             for (int j = 0; j < n; j++) {
                 const uint32_t pos = wpos[j];
-                float g[16];
+                float g[10];
 #pragma unroll
-                for (int i = 0; i < 16; i++) g[i] = 0.f;
+                for (int i = 0; i < 10; i++) g[i] = 0.f;
                 bool any = false;
                 const float2 m = wxy[j];
                 const float4 cr = wrgb[j];
@@ -451,7 +479,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(Bl
                     }
                 }
                 if (__ballot_sync(kFull, any) == 0u) continue;
-                const float sum = warp_reduce_scatter16(g, lane);
+                const float sum = warp_reduce_scatter10(g, lane);
                 if (adder) {
                     // the conic gradients sum terms weighted by dx^2 ~ 1e4 px^2 of both
                     // signs: they are added across warps in double precision
@@ -504,17 +532,22 @@ void launch_blend_forward(const BlendArgs& a, int* counter, float* img, float* f
     const bool sampled = a.s_off != nullptr;
     // sampled mode: the number of runs is only known on the device; launch a
     // full persistent grid
-    const bool depth = a.depth_out != nullptr;
+    const bool depth = a.depth_out != nullptr, stats = pixel_stats != nullptr;
     const long long items = sampled ? (1LL << 40) : a.tiles * a.strips;
-#define MVGS_BF1(P, S, B, D)                                                                                 \
-    blend_forward_kernel<P, S, B, D><<<grid_for(blend_forward_kernel<P, S, B, D>, items), 32 * WARPS_PER_BLOCK, 0, \
-                                       s>>>(a, counter, img, final_T, n_contrib, pixel_stats)
-#define MVGS_BF(P, S, B)              \
-    do {                              \
-        if (depth)                    \
-            MVGS_BF1(P, S, B, true);  \
-        else                          \
-            MVGS_BF1(P, S, B, false); \
+#define MVGS_BF1(P, S, B, D, ST)                                                                  \
+    blend_forward_kernel<P, S, B, D, ST><<<grid_for(blend_forward_kernel<P, S, B, D, ST>, items),          \
+                                           32 * WARPS_PER_BLOCK, 0, s>>>(a, counter, img, final_T, n_contrib, \
+                                                                         pixel_stats)
+#define MVGS_BF(P, S, B)                        \
+    do {                                        \
+        if (depth && stats)                     \
+            MVGS_BF1(P, S, B, true, true);      \
+        else if (depth)                         \
+            MVGS_BF1(P, S, B, true, false);     \
+        else if (stats)                         \
+            MVGS_BF1(P, S, B, false, true);     \
+        else                                    \
+            MVGS_BF1(P, S, B, false, false);    \
     } while (0)
 #define MVGS_BF2(P, B)              \
     do {                            \

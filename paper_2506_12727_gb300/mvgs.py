@@ -63,6 +63,7 @@ class Sampling(ctypes.Structure):
 FLAG_MASKED_PARTIAL = 1
 FLAG_DEPTH = 2
 FLAG_CAPTURABLE = 4
+FLAG_PIXEL_STATS = 8
 
 
 class DensifyParams(ctypes.Structure):
@@ -487,12 +488,12 @@ class Rasterizer:
         else:
             self.state = self.workspace = self.layout = None
 
-    def _cfg(self, masked=False, depth=False):
-        if not masked and not depth and not self.capturable:
+    def _cfg(self, masked=False, depth=False, stats=False):
+        if not masked and not depth and not stats and not self.capturable:
             return self.cfg
         cfg = Config.from_buffer_copy(self.cfg)
         cfg.flags = (FLAG_MASKED_PARTIAL if masked else 0) | (FLAG_DEPTH if depth else 0) | \
-            (FLAG_CAPTURABLE if self.capturable else 0)
+            (FLAG_CAPTURABLE if self.capturable else 0) | (FLAG_PIXEL_STATS if stats else 0)
         return cfg
 
     def sample_set(self, group: int, seed: int, stream=None, cell=(1, 1)) -> SampleSet:
@@ -511,11 +512,12 @@ class Rasterizer:
         return (tw, (32 // tw) * ppt)
 
     def forward(self, scene_c, images=None, stream=None, samples: SampleSet | None = None, masked=False,
-                depth=False):
+                depth=False, stats=False):
         """Full render, or with `samples` only the sampled pixels (Alg. 3; with
         masked=True through the full strips with idle lanes, Fig. 3b).  With
         depth=True the expected depth of each rendered pixel is written too
-        (records()["depth_acc"])."""
+        (records()["depth_acc"]); with stats=True the per-pixel statistics
+        (records()["pixel_stats"]: where the pixel stopped, Gaussians blended)."""
         n = scene_c.n
         if images is None:
             images = torch.empty(3 * self.pixels, dtype=torch.float32, device=self.device)
@@ -525,22 +527,23 @@ class Rasterizer:
             if self.state is None or n != self.n:
                 raise MvgsError(EINVAL, "a capturable rasterizer needs reserve(n, records, keys) first")
             if samples is None:
-                render_views(scene_c, self.cams_c, self._cfg(False, depth), self.cap, images, self.state,
+                render_views(scene_c, self.cams_c, self._cfg(False, depth, stats), self.cap, images, self.state,
                              self.workspace, stream)
             else:
-                render_views_sampled(scene_c, self.cams_c, self._cfg(masked, depth), self.cap, samples, images,
-                                     self.state, self.workspace, stream)
+                render_views_sampled(scene_c, self.cams_c, self._cfg(masked, depth, stats), self.cap, samples,
+                                     images, self.state, self.workspace, stream)
             self.needed = Capacity(self.cap.records, self.cap.keys)
             return images
         self._ensure(n, max(self.cap.records, 1), max(self.cap.keys, 1))
         for _ in range(4):
             try:
                 if samples is None:
-                    self.needed = render_views(scene_c, self.cams_c, self._cfg(False, depth), self.cap, images,
-                                               self.state, self.workspace, stream)
+                    self.needed = render_views(scene_c, self.cams_c, self._cfg(False, depth, stats), self.cap,
+                                               images, self.state, self.workspace, stream)
                 else:
-                    self.needed = render_views_sampled(scene_c, self.cams_c, self._cfg(masked, depth), self.cap,
-                                                       samples, images, self.state, self.workspace, stream)
+                    self.needed = render_views_sampled(scene_c, self.cams_c, self._cfg(masked, depth, stats),
+                                                       self.cap, samples, images, self.state, self.workspace,
+                                                       stream)
                 return images
             except MvgsError as e:
                 if e.status != ENOSPACE or e.needed is None:

@@ -93,7 +93,7 @@ def test_bad_arguments_are_rejected(lib):
         lib.render_layout(10, bad, cfg, lib.Capacity(10, 10))
     assert e.value.status == lib.EINVAL
     assert "empty image" in lib.last_error()
-    cfg.flags = 8  # only bits 1, 2 and 4 (masked partial, depth, capturable) are defined
+    cfg.flags = 16  # only bits 1, 2, 4 and 8 (masked partial, depth, capturable, pixel stats) are defined
     with pytest.raises(lib.MvgsError):
         lib.render_layout(10, cc, cfg, lib.Capacity(10, 10))
     cfg.flags = lib.FLAG_MASKED_PARTIAL

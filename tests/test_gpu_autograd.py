@@ -83,7 +83,7 @@ def _tile_hash(rec):
 
 def _render_with_stats(setup, params):
     mvgs, rz = setup["mvgs"], setup["rz"]
-    img = rz.forward(mvgs.make_scene(params, setup["scene"].sh_degree)).clone()
+    img = rz.forward(mvgs.make_scene(params, setup["scene"].sh_degree), stats=True).clone()
     rec = rz.records()
     stats = torch.cat([rec["pixel_stats"], rec["n_contrib"][:, None]], 1).clone()
     return img, stats, _tile_hash(rec)
