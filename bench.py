@@ -565,11 +565,11 @@ def stage_work(rz, needed, V, pixels, blended):
 
 
 # DRAM bytes (read + write) per blended pair of the blend kernels, from the ncu
-# --set full capture of one view of this scene (profiles/blend_kernels_
-# multiview_500k_1x1264x832_16x64.md: forward 22.62 MB, backward 50.35 MB over
-# 103,536,139 blended pairs); a full launch's traffic is taken in proportion
-# to its blended pairs.  Valid for the kernels as captured.
-DRAM_BYTES_PER_BLENDED = {"blend_forward": 22.622464e6 / 103536139, "blend_backward": 50.347776e6 / 103536139}
+# capture of the benchmark step (profiles/blend_kernels_multiview_500k_
+# 4x1264x832_16x64.md: forward 122.95 MB, backward 216.30 MB per launch over
+# 449,569,394 blended pairs); a launch of another workload is taken in
+# proportion to its blended pairs.  Valid for the kernels as captured.
+DRAM_BYTES_PER_BLENDED = {"blend_forward": 122.95e6 / 449569394, "blend_backward": 216.30e6 / 449569394}
 
 
 def roofline(stages, args, needed, rz, clk, V, pixels, blended):
@@ -604,7 +604,7 @@ def roofline(stages, args, needed, rz, clk, V, pixels, blended):
     d["traffic"] = None
     if dom in DRAM_BYTES_PER_BLENDED and blended:
         d["traffic"] = int(DRAM_BYTES_PER_BLENDED[dom] * blended)
-        d["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the one-view capture, "
+        d["traffic_source"] = ("ncu dram__bytes (read + write) of the kernel in the benchmark step, "
                                "scaled by blended pairs")
     if d["bound"] == "alu":
         per = FWD_FLOP_PER_BLENDED if dom == "blend_forward" else BWD_FLOP_PER_BLENDED
