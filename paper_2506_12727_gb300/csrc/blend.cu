@@ -162,16 +162,16 @@ __device__ __forceinline__ bool next_work(const BlendArgs& a, int* counter, int 
 }
 
 // Resident blocks per SM the forward is compiled for: six (at most 80
-// registers) for strips of 4 pixels per lane without the depth and statistics
-// outputs, where the state fits without spilling and the extra warps hide
-// more latency than the registers given up cost; no bound elsewhere (more
-// state there, and a bound spills it).
-constexpr int fwd_min_blocks(int ppt, bool sampled, bool extra) { return ppt == 4 && !sampled && !extra ? 6 : 1; }
+// registers) for 4 pixels per lane without the depth and statistics outputs
+// (strips and sample runs), where the extra warps hide more latency than the
+// registers given up cost (3-4% faster); no bound elsewhere (more state
+// there, and a bound spills it).
+constexpr int fwd_min_blocks(int ppt, bool extra) { return ppt == 4 && !extra ? 6 : 1; }
 
 // DEPTH: also the expected depth per pixel; STATS: also the per-pixel
 // statistics (list position where the pixel stopped, Gaussians blended).
 template <int PPT, bool SAMPLED, int WBATCH, bool DEPTH, bool STATS>
-__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, fwd_min_blocks(PPT, SAMPLED, DEPTH || STATS))
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, fwd_min_blocks(PPT, DEPTH || STATS))
     blend_forward_kernel(BlendArgs a, int* __restrict__ counter,
                                                                              float* __restrict__ img,
                                                                              float* __restrict__ final_T,
