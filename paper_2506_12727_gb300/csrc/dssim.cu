@@ -104,19 +104,33 @@ __global__ void __launch_bounds__(256) dssim_forward_kernel(Views vw, const floa
     __syncthreads();
     float ssim = 0.f, l1 = 0.f;
     const int c = threadIdx.x % TSX;
+    // a thread's ROWS consecutive output rows share ROWS + TAPS - 1 staged rows:
+    // each staged value is read once and used for every output it reaches
+    const int r0 = (threadIdx.x / TSX) * ROWS;
+    float mv[ROWS][5];
+#pragma unroll
+    for (int q = 0; q < ROWS; q++)
+#pragma unroll
+        for (int i = 0; i < 5; i++) mv[q][i] = 0.f;
+#pragma unroll
+    for (int k = 0; k < ROWS + TAPS - 1; k++) {
+        float hv[5];
+#pragma unroll
+        for (int i = 0; i < 5; i++) hv[i] = h[i][r0 + k][c];
+#pragma unroll
+        for (int q = 0; q < ROWS; q++) {
+            const int t = k - q;
+            if (t >= 0 && t < TAPS) {
+                const float w = vw.w[t];
+#pragma unroll
+                for (int i = 0; i < 5; i++) mv[q][i] += w * hv[i];
+            }
+        }
+    }
 #pragma unroll
     for (int q = 0; q < ROWS; q++) {
-        const int r = threadIdx.x / TSX + 8 * q;
-        float m1 = 0.f, m2 = 0.f, m11 = 0.f, m22 = 0.f, m12 = 0.f;
-#pragma unroll
-        for (int k = 0; k < TAPS; k++) {
-            const float w = vw.w[k];
-            m1 += w * h[0][r + k][c];
-            m2 += w * h[1][r + k][c];
-            m11 += w * h[2][r + k][c];
-            m22 += w * h[3][r + k][c];
-            m12 += w * h[4][r + k][c];
-        }
+        const int r = r0 + q;
+        const float m1 = mv[q][0], m2 = mv[q][1], m11 = mv[q][2], m22 = mv[q][3], m12 = mv[q][4];
         const int x = p.x0 + c, y = p.y0 + r;
         if (x < p.W && y < p.H) {
             const float t11 = m11 - m1 * m1, t22 = m22 - m2 * m2, t12 = m12 - m1 * m2;
@@ -189,19 +203,30 @@ __global__ void __launch_bounds__(256) dssim_backward_kernel(Views vw, const flo
     __syncthreads();
     const int c = threadIdx.x % TSX;
     const float inv_n = 1.f / (3.f * (float)p.H * (float)p.W);
+    const int r0 = (threadIdx.x / TSX) * ROWS;
+    float bv[ROWS][3];
+#pragma unroll
+    for (int q = 0; q < ROWS; q++) bv[q][0] = bv[q][1] = bv[q][2] = 0.f;
+#pragma unroll
+    for (int k = 0; k < ROWS + TAPS - 1; k++) {
+        const float h0 = h[0][r0 + k][c], h1 = h[1][r0 + k][c], h2 = h[2][r0 + k][c];
+#pragma unroll
+        for (int q = 0; q < ROWS; q++) {
+            const int t = k - q;
+            if (t >= 0 && t < TAPS) {
+                const float w = vw.w[t];
+                bv[q][0] += w * h0;
+                bv[q][1] += w * h1;
+                bv[q][2] += w * h2;
+            }
+        }
+    }
 #pragma unroll
     for (int q = 0; q < ROWS; q++) {
-        const int r = threadIdx.x / TSX + 8 * q;
+        const int r = r0 + q;
         const int x = p.x0 + c, y = p.y0 + r;
         if (x >= p.W || y >= p.H) continue;
-        float B1 = 0.f, B11 = 0.f, B12 = 0.f;
-#pragma unroll
-        for (int k = 0; k < TAPS; k++) {
-            const float w = vw.w[k];
-            B1 += w * h[0][r + k][c];
-            B11 += w * h[1][r + k][c];
-            B12 += w * h[2][r + k][c];
-        }
+        const float B1 = bv[q][0], B11 = bv[q][1], B12 = bv[q][2];
         const long long o = p.plane + (long long)y * p.W + x;
         const float i1 = img[o], i2 = tgt[o];
         const float diff = i1 - i2;
