@@ -330,3 +330,28 @@ def test_results_do_not_depend_on_the_batch_size(cuda_lib):
     for g in grads[1:]:
         for k in PARAMS:
             assert_close_frac(g[k], grads[0][k], 1e-3, 1e-6 * np.abs(grads[0][k]).max(), k)
+
+
+def test_optional_outputs_do_not_change_the_render(cuda_lib):
+    # the depth and statistics outputs are separate kernel variants: the image,
+    # final T and last contributors must not depend on which one runs
+    scene, cams = CASES["multiview_sh3_ragged"]
+    params = scene_to_device(scene)
+    sc = cuda_lib.make_scene(params, scene.sh_degree)
+    rz = cuda_lib.Rasterizer(cams, tile=(16, 32), bg=(0.1, 0.2, 0.3))
+    runs = []
+    for depth, stats in ((False, False), (True, False), (False, True), (True, True)):
+        img = rz.forward(sc, depth=depth, stats=stats).clone()
+        rec = rz.records()
+        runs.append((img, rec["final_T"].clone(), rec["n_contrib"].clone(),
+                     rec["pixel_stats"].clone() if stats else None))
+    for img, T, last, _ in runs[1:]:
+        assert torch.equal(img, runs[0][0])
+        assert torch.equal(T, runs[0][1])
+        assert torch.equal(last, runs[0][2])
+    # the statistics agree between the two variants that write them, and the
+    # blended count never exceeds the list position of the last contributor
+    assert torch.equal(runs[2][3], runs[3][3])
+    st = runs[2][3].to(torch.int64)
+    assert bool((st[:, 1] <= runs[2][2].to(torch.int64)).all())
+    assert bool((runs[2][2].to(torch.int64) <= st[:, 0]).all())
