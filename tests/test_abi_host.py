@@ -105,3 +105,11 @@ def test_dssim_workspace_size(lib):
     n = lib.dssim_workspace_size(hw)
     P = 832 * 1264 + 35
     assert n >= 3 * 3 * P * 4
+
+
+def test_flag_constants_match_header(lib):
+    src = open(os.path.join(ROOT, "include", "mvgs.h")).read()
+    flags = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define MVGS_(FLAG_[A-Z_]+)\s+(\d+)u", src)}
+    assert flags == {"FLAG_MASKED_PARTIAL": 1, "FLAG_DEPTH": 2, "FLAG_CAPTURABLE": 4, "FLAG_PIXEL_STATS": 8}
+    for name, value in flags.items():
+        assert getattr(lib, name) == value, name
