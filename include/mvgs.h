@@ -265,9 +265,10 @@ mvgs_status mvgs_partial_samples(const mvgs_camera* cams, int32_t V, const mvgs_
                                  size_t workspace_bytes, mvgs_stream stream);
 
 /* mvgs_render_views restricted to a sample set: writes the images,
- * final_T, n_contrib and pixel_stats of the sampled pixels only (every other
- * pixel of `images` and of those state arrays is left as it was).  A sampled
- * pixel gets exactly the value the full render gives it. */
+ * final_T, n_contrib (and with the flags the depth and pixel statistics) of
+ * the sampled pixels only (every other pixel of `images` and of those state
+ * arrays is left as it was).  A sampled pixel gets exactly the value the full
+ * render gives it. */
 mvgs_status mvgs_render_views_sampled(const mvgs_scene* scene, const mvgs_camera* cams, int32_t V,
                                       const mvgs_config* cfg, const mvgs_capacity* cap, const mvgs_samples* samples,
                                       float* images, void* state, size_t state_bytes, void* workspace,
