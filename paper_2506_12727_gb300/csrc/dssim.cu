@@ -27,7 +27,7 @@ constexpr int TSX = 32, TSY = 32;
 constexpr int ROWS = TSY / 8;  // output rows per thread
 constexpr int RADIUS = 5;            // 11 taps
 constexpr int TAPS = 2 * RADIUS + 1;
-constexpr int HSX = TSX + 2 * RADIUS, HSY = TSY + 2 * RADIUS;  // staged 42 x 26
+constexpr int HSX = TSX + 2 * RADIUS, HSY = TSY + 2 * RADIUS;  // staged 42 x 42
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
 constexpr int kMaxViews = 64;
@@ -74,7 +74,8 @@ __global__ void __launch_bounds__(256) dssim_forward_kernel(Views vw, const floa
                                                            float* __restrict__ dm1, float* __restrict__ dm11,
                                                            float* __restrict__ dm12, float2* __restrict__ bsum,
                                                            long long blk_offset) {
-    __shared__ float s1[HSY][HSX + 1], s2[HSY][HSX + 1];
+    // rows of 44 floats: 16-byte aligned, for the vector reads of the row pass
+    __shared__ __align__(16) float s1[HSY][HSX + 2], s2[HSY][HSX + 2];
     __shared__ float h[5][HSY][TSX + 1];
     __shared__ float red[2][8];
     const BlockPos p = block_pos(vw);
@@ -87,19 +88,33 @@ __global__ void __launch_bounds__(256) dssim_forward_kernel(Views vw, const floa
         s2[r][c] = in ? tgt[o] : 0.f;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < HSY * TSX; i += blockDim.x) {
-        const int r = i / TSX, c = i % TSX;
-        float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+    // row pass, four adjacent outputs per item: their 14 inputs come in four
+    // 16-byte reads instead of 44 scalar ones
+    for (int i = threadIdx.x; i < HSY * (TSX / 4); i += blockDim.x) {
+        const int r = i / (TSX / 4), c0 = 4 * (i % (TSX / 4));
+        float x1[16], x2[16];
 #pragma unroll
-        for (int k = 0; k < TAPS; k++) {
-            const float x1 = s1[r][c + k], x2 = s2[r][c + k], w = vw.w[k];
-            a += w * x1;
-            b += w * x2;
-            aa += w * x1 * x1;
-            bb += w * x2 * x2;
-            ab += w * x1 * x2;
+        for (int q = 0; q < 4; q++) {
+            const float4 u = reinterpret_cast<const float4*>(&s1[r][c0])[q];
+            const float4 v = reinterpret_cast<const float4*>(&s2[r][c0])[q];
+            x1[4 * q] = u.x; x1[4 * q + 1] = u.y; x1[4 * q + 2] = u.z; x1[4 * q + 3] = u.w;
+            x2[4 * q] = v.x; x2[4 * q + 1] = v.y; x2[4 * q + 2] = v.z; x2[4 * q + 3] = v.w;
         }
-        h[0][r][c] = a; h[1][r][c] = b; h[2][r][c] = aa; h[3][r][c] = bb; h[4][r][c] = ab;
+#pragma unroll
+        for (int o = 0; o < 4; o++) {
+            float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+#pragma unroll
+            for (int k = 0; k < TAPS; k++) {
+                const float u = x1[o + k], v = x2[o + k], w = vw.w[k];
+                a += w * u;
+                b += w * v;
+                aa += w * u * u;
+                bb += w * v * v;
+                ab += w * u * v;
+            }
+            const int c = c0 + o;
+            h[0][r][c] = a; h[1][r][c] = b; h[2][r][c] = aa; h[3][r][c] = bb; h[4][r][c] = ab;
+        }
     }
     __syncthreads();
     float ssim = 0.f, l1 = 0.f;
@@ -175,7 +190,7 @@ __global__ void __launch_bounds__(256) dssim_backward_kernel(Views vw, const flo
                                                             const float* __restrict__ dm11,
                                                             const float* __restrict__ dm12, float lambda,
                                                             float inv_views, float* __restrict__ dimg) {
-    __shared__ float s[3][HSY][HSX + 1];
+    __shared__ __align__(16) float s[3][HSY][HSX + 2];
     __shared__ float h[3][HSY][TSX + 1];
     const BlockPos p = block_pos(vw);
     for (int i = threadIdx.x; i < HSY * HSX; i += blockDim.x) {
@@ -188,17 +203,29 @@ __global__ void __launch_bounds__(256) dssim_backward_kernel(Views vw, const flo
         s[2][r][c] = in ? dm12[o] : 0.f;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < HSY * TSX; i += blockDim.x) {
-        const int r = i / TSX, c = i % TSX;
-        float a = 0.f, b = 0.f, d = 0.f;
+    for (int i = threadIdx.x; i < HSY * (TSX / 4); i += blockDim.x) {
+        const int r = i / (TSX / 4), c0 = 4 * (i % (TSX / 4));
+        float x[3][16];
 #pragma unroll
-        for (int k = 0; k < TAPS; k++) {
-            const float w = vw.w[k];
-            a += w * s[0][r][c + k];
-            b += w * s[1][r][c + k];
-            d += w * s[2][r][c + k];
+        for (int m = 0; m < 3; m++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const float4 u = reinterpret_cast<const float4*>(&s[m][r][c0])[q];
+                x[m][4 * q] = u.x; x[m][4 * q + 1] = u.y; x[m][4 * q + 2] = u.z; x[m][4 * q + 3] = u.w;
+            }
+#pragma unroll
+        for (int o = 0; o < 4; o++) {
+            float a = 0.f, b = 0.f, d = 0.f;
+#pragma unroll
+            for (int k = 0; k < TAPS; k++) {
+                const float w = vw.w[k];
+                a += w * x[0][o + k];
+                b += w * x[1][o + k];
+                d += w * x[2][o + k];
+            }
+            const int c = c0 + o;
+            h[0][r][c] = a; h[1][r][c] = b; h[2][r][c] = d;
         }
-        h[0][r][c] = a; h[1][r][c] = b; h[2][r][c] = d;
     }
     __syncthreads();
     const int c = threadIdx.x % TSX;

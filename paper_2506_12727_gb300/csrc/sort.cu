@@ -571,13 +571,67 @@ __global__ void diff_to_counts_kernel(const DevCam* __restrict__ cams, int* __re
 }
 
 // Sort key of a tile for the blend's processing order: longest lists first.
-__global__ void tile_order_keys_kernel(const long long* __restrict__ ranges, long long tiles,
-                                       uint32_t* __restrict__ keys, uint32_t* __restrict__ ids) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= tiles) return;
-    const long long len = (ranges[2 * t + 1] - ranges[2 * t]) >> 2;
-    keys[t] = 0xffffu - (uint32_t)(len < 0xffff ? len : 0xffff);
-    ids[t] = (uint32_t)t;
+// Blend processing order: tiles by decreasing list length, in 256 length
+// classes (8 per octave: the exponent and three mantissa bits of length + 1),
+// tile id order inside a class; the persistent blend kernels take the longest
+// lists first so that no heavy tile is left for the end of the queue.  One
+// block sorts all tiles by counting in shared memory (one launch instead of a
+// radix sort's ten).
+constexpr int TO_THREADS = 1024;
+constexpr int TO_WARPS = TO_THREADS / 32;
+
+__device__ __forceinline__ uint32_t length_class(long long len) {
+    const unsigned long long v = (unsigned long long)(len > 0 ? len : 0) + 1ull;
+    const int e = 63 - __clzll((long long)v);
+    const uint32_t m = e >= 3 ? (uint32_t)(v >> (e - 3)) & 7u : (uint32_t)(v << (3 - e)) & 7u;
+    const uint32_t b = 8u * (uint32_t)e + m;  // grows with the length
+    return 255u - (b < 255u ? b : 255u);      // 0: the longest lists
+}
+
+__global__ void __launch_bounds__(TO_THREADS) tile_order_kernel(const long long* __restrict__ ranges, long long tiles,
+                                                                uint32_t* __restrict__ order) {
+    __shared__ uint32_t off[256];                // per class: next output position
+    __shared__ uint32_t wcnt[TO_WARPS][256];     // per warp and class, within a chunk
+    __shared__ uint32_t buf[33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    auto cls = [&](long long t) { return length_class(ranges[2 * t + 1] - ranges[2 * t]); };
+    if (threadIdx.x < 256) off[threadIdx.x] = 0;
+    __syncthreads();
+    for (long long t = threadIdx.x; t < tiles; t += TO_THREADS) atomicAdd(&off[cls(t)], 1u);
+    __syncthreads();
+    uint32_t total;
+    const uint32_t c0 = threadIdx.x < 256 ? off[threadIdx.x] : 0u;
+    const uint32_t ex = block_exclusive_scan<uint32_t>(c0, buf, total);
+    if (threadIdx.x < 256) off[threadIdx.x] = ex;
+    __syncthreads();
+    // stable scatter, chunk by chunk in tile order: rank inside the warp by
+    // matching classes, then add the counts of the warps before
+    for (long long base = 0; base < tiles; base += TO_THREADS) {
+        const long long t = base + threadIdx.x;
+        const bool valid = t < tiles;
+        const uint32_t c = valid ? cls(t) : 256u;
+        const uint32_t peers = __match_any_sync(kFull, c);
+        for (int i = lane; i < 256; i += 32) wcnt[warp][i] = 0;
+        __syncwarp();
+        if (valid && (peers & lt) == 0) wcnt[warp][c] = (uint32_t)__popc(peers);
+        __syncthreads();
+        if (threadIdx.x < 256) {
+            uint32_t run = off[threadIdx.x];
+            for (int w = 0; w < TO_WARPS; w++) {
+                const uint32_t n = wcnt[w][threadIdx.x];
+                wcnt[w][threadIdx.x] = run;
+                run += n;
+            }
+            off[threadIdx.x] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            const uint32_t pos = wcnt[warp][c] + (uint32_t)__popc(peers & lt);
+            if ((long long)pos < tiles) order[pos] = (uint32_t)t;
+        }
+        __syncthreads();
+    }
 }
 
 // Ranges are clamped to the entries that were generated (all of them unless
@@ -708,22 +762,12 @@ void tile_sort(const uint32_t* order, const unsigned long long* tile_off, Count 
     }
 }
 
-size_t tile_order_temp_bytes(long long tiles) {
-    const size_t a = ((size_t)(tiles > 0 ? tiles : 1) * sizeof(uint32_t) + 255) / 256 * 256;
-    return 4 * a + radix_temp_bytes((uint64_t)(tiles > 0 ? tiles : 1));
-}
+size_t tile_order_temp_bytes(long long) { return 256; }
 
-void tile_order(const long long* ranges, long long tiles, uint32_t* order, void* tmp, cudaStream_t s) {
+void tile_order(const long long* ranges, long long tiles, uint32_t* order, void*, cudaStream_t s) {
     if (tiles <= 0) return;
-    const size_t a = ((size_t)tiles * sizeof(uint32_t) + 255) / 256 * 256;
-    char* base = static_cast<char*>(tmp);
-    uint32_t* ka = reinterpret_cast<uint32_t*>(base);
-    uint32_t* ia = reinterpret_cast<uint32_t*>(base + a);
-    uint32_t* kb = reinterpret_cast<uint32_t*>(base + 2 * a);
-    uint32_t* ib = reinterpret_cast<uint32_t*>(base + 3 * a);
-    tile_order_keys_kernel<<<(unsigned)ceil_div_u64((uint64_t)tiles, 256), 256, 0, s>>>(ranges, tiles, ka, ia);
+    tile_order_kernel<<<1, TO_THREADS, 0, s>>>(ranges, tiles, order);
     note_launches(1);
-    radix_sort_pairs(ka, ia, kb, ib, order, (uint64_t)tiles, 16, base + 4 * a, s);
 }
 
 static long long diff_cells(const DevCam* host_cams, int V) {
