@@ -1,8 +1,8 @@
 // Tile-based alpha blending (Eq. 1) and its backward.
 //
-// The supplement allocates "one block for each viewpoint" per tile, and
-// Alg. 2 has a tile's threads fetch its depth-sorted Gaussians into shared
-// memory batch by batch and blend them.  Here the unit of work is a strip of
+// In the supplement's rasterizer every (tile, view) pair gets its own thread
+// block, and Alg. 2 has a tile's threads fetch its depth-sorted Gaussians
+// into shared memory batch by batch and blend them.  Here the unit of work is a strip of
 // a (tile, view) pair -- tile_w columns by (32 / tile_w) * PPT rows -- owned by
 // one warp: each lane owns PPT pixels of one column, the warp stages batches
 // of the tile's list in its own slice of shared memory, and leaves the strip
