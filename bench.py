@@ -618,14 +618,25 @@ def roofline(stages, args, needed, rz, clk, V, pixels, blended):
 # ---------------------------------------------------------------------------
 # the CPU oracle
 # ---------------------------------------------------------------------------
+_ORACLE_INPUTS = {}
+
+
+def _oracle_inputs(workload):
+    """The seeded scene, cameras and targets of a workload (generated once
+    per process: generation is not part of a sample)."""
+    if workload not in _ORACLE_INPUTS:
+        scene, cams, _ = synth.workload(workload)
+        _ORACLE_INPUTS[workload] = (scene, cams, synth.make_targets(cams))
+    return _ORACLE_INPUTS[workload]
+
+
 def oracle_sample(workload, view=0, window=None):
     """One bounded sample of the workload on the oracle: forward + loss +
     backward of one view (optionally a pixel window of it).  Returns
     (seconds, fraction of a full view the sample covers)."""
     import oracle
-    scene, cams, extra = synth.workload(workload)
+    scene, cams, targets = _oracle_inputs(workload)
     c1 = cams.subset([view])
-    targets = synth.make_targets(cams)
     t0 = time.perf_counter()
     fw = oracle.forward(scene, c1, (16, 16), window=window)
     H, W = int(c1.height[0]), int(c1.width[0])
@@ -678,9 +689,15 @@ def cpu_baseline(workload):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    scene, cams, extra = synth.workload(args.workload)
+    scene, cams, _ = _oracle_inputs(args.workload)
     W, H = int(cams.width[0]), int(cams.height[0])
-    win = np.array([[W // 2 - 128, H // 2 - 128, W // 2 + 128, H // 2 + 128]])
+    # each step is one window of view 0, sized so that the whole run stays
+    # within about two and a half minutes of one core (a 256x256 window takes
+    # ~3.3 s, 128x128 ~1.4 s, 64x64 ~0.8 s on the benchmark scene)
+    per_step = 150.0 / max(1, args.steps + args.warmup)
+    side = 256 if per_step >= 3.5 else (128 if per_step >= 1.5 else 64)
+    side = min(side, W, H)
+    win = np.array([[W // 2 - side // 2, H // 2 - side // 2, W // 2 + side // 2, H // 2 + side // 2]])
     for _ in range(args.warmup):
         oracle_sample(args.workload, window=win)
     times = []
@@ -690,7 +707,7 @@ def run_reference(args, rank, world):
         times.append(dt)
     ms = 1e3 * sum(times) / len(times)
     value = frac / (ms / 1e3)
-    sample = f"256x256 window at the centre of view 0 of {args.workload}, forward + loss + backward, one thread"
+    sample = f"{side}x{side} window at the centre of view 0 of {args.workload}, forward + loss + backward, one thread"
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
