@@ -138,9 +138,13 @@ class Server:
             pixels += r.pixels
         return batch
 
-    def _worker(self, index):
+    def _worker_stream(self):
+        """The worker's own CUDA stream, on the server's device."""
         torch.cuda.set_device(self._dev_index)
-        stream = torch.cuda.Stream()
+        return torch.cuda.Stream()
+
+    def _worker(self, index):
+        stream = self._worker_stream()
         rz = None
         while True:
             with self.cv:
