@@ -193,3 +193,54 @@ def poisson_requests(n_requests: int, rate_hz: float = 200.0, seed: int = SEED_R
         res = [SERVE_RES[j] for j in rng.integers(0, len(SERVE_RES), size=nv)]
         reqs.append({"t": float(t[i]), "resolutions": res, "cam_seed": int(rng.integers(0, 2**31 - 1))})
     return reqs
+
+
+def off_axis_scene(n_out: int, n_in: int, sh_degree: int = 1, W: int = 64, H: int = 48, fov_deg: float = 60.0,
+                   seed: int = 40):
+    """Gaussians seen at steep angles, for the projection's behaviour far
+    off the optical axis: two cameras facing each other (the first at the
+    origin looking down +z, the second at z = 6 looking down -z), `n_out`
+    Gaussians whose view-angle tangents in the first camera are 1.4 to 1.9
+    times the half-FOV tangent on one or both axes (so their centres project
+    outside the image), with scales large enough that they still reach
+    into it, and `n_in` ordinary Gaussians inside the view.  Depths 1.8 to
+    4.2 in both cameras."""
+    rng = np.random.default_rng(seed)
+    f = (W / 2.0) / math.tan(math.radians(fov_deg) / 2.0)
+    Lx, Ly = (W / 2.0) / f, (H / 2.0) / f
+    n = n_out + n_in
+    z = rng.uniform(1.8, 4.2, size=n)
+    ux = rng.uniform(-0.6, 0.6, size=n) * Lx
+    uy = rng.uniform(-0.6, 0.6, size=n) * Ly
+    # which axes are far out: x only, y only, or both, with either sign
+    kind = rng.integers(0, 3, size=n_out)
+    sx = rng.choice([-1.0, 1.0], size=n_out)
+    sy = rng.choice([-1.0, 1.0], size=n_out)
+    far_x = rng.uniform(1.4, 1.9, size=n_out) * Lx * sx
+    far_y = rng.uniform(1.4, 1.9, size=n_out) * Ly * sy
+    ux[:n_out] = np.where(kind != 1, far_x, ux[:n_out])
+    uy[:n_out] = np.where(kind != 0, far_y, uy[:n_out])
+    means = np.stack([ux * z, uy * z, z], 1)
+    log_scales = np.empty((n, 3))
+    log_scales[:n_out] = rng.normal(np.log(0.6), 0.2, size=(n_out, 3)) + np.log(z[:n_out, None] / 3.0)
+    log_scales[n_out:] = rng.normal(-2.5, 0.4, size=(n_in, 3))
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    logits = rng.normal(0.5, 1.0, size=n)
+    k = (sh_degree + 1) ** 2
+    sh = np.zeros((n, k, 3))
+    sh[:, 0, :] = rng.uniform(0.0, 1.0, size=(n, 3))
+    if k > 1:
+        sh[:, 1:, :] = rng.normal(0.0, 0.05, size=(n, k - 1, 3))
+    f32 = np.float32
+    scene = Scene(means.astype(f32), log_scales.astype(f32), q.astype(f32), logits.astype(f32), sh.astype(f32),
+                  sh_degree)
+    vm = np.zeros((2, 3, 4))
+    vm[0, :, :3] = np.eye(3)
+    vm[1, :, :3] = np.diag([-1.0, 1.0, -1.0])
+    vm[1, :, 3] = [0.0, 0.0, 6.0]
+    # the second camera's far Gaussians: depth 6 - z must stay in 1.8 .. 4.2
+    cams = Cameras(np.full(2, W, np.int32), np.full(2, H, np.int32), np.full(2, f, f32), np.full(2, f, f32),
+                   np.full(2, W / 2.0, f32), np.full(2, H / 2.0, f32), vm.astype(f32),
+                   np.array([[0, 0, 0], [0, 0, 6]], f32), np.full(2, 0.2, f32))
+    return scene, cams

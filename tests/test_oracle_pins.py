@@ -396,3 +396,164 @@ def test_tile_rect_covers_every_pixel_a_gaussian_can_reach():
                 x0, y0, x1, y1 = P["rect"][r]
                 tx, ty = xs[hit] // tile[0], ys[hit] // tile[1]
                 assert np.all((tx >= x0) & (tx < x1) & (ty >= y0) & (ty < y1)), (v, g)
+
+
+# ---------------------------------------------------------------------------
+# the projection far off the optical axis (guard band of the Jacobian)
+# ---------------------------------------------------------------------------
+def _camera_space(sc, cams, v):
+    vm = cams.viewmat[v].astype(np.float64)
+    return sc.means.astype(np.float64) @ vm[:, :3].T + vm[:, 3]
+
+
+def _band(cams, v):
+    """The guard band of the 3DGS projection: 1.3 x the half-FOV tangents."""
+    return (1.3 * 0.5 * float(cams.width[v]) / float(cams.fx[v]),
+            1.3 * 0.5 * float(cams.height[v]) / float(cams.fy[v]))
+
+
+def test_guard_band_covariance_is_the_projection_at_the_band_edge():
+    """Beyond 1.3 x the half-FOV tangent the EWA Jacobian is taken at the
+    band's edge (3DGS reading): the projected covariance of a Gaussian out
+    there equals that of the same Gaussian moved, at the same depth, onto the
+    edge -- where it is the plain perspective map, checked against Monte
+    Carlo samples pushed through it -- while its projected mean is the
+    pinhole projection of the unmoved mean."""
+    sc, cams = synth.off_axis_scene(24, 0, sh_degree=0, seed=41)
+    sc.log_scales[:] = np.random.default_rng(42).normal(-4.0, 0.3, size=sc.log_scales.shape).astype(np.float32)
+    N = sc.n
+    P = oracle.project(sc, cams, (16, 16))
+    t = _camera_space(sc, cams, 0)  # the first camera is the identity: world = camera
+    limx, limy = _band(cams, 0)
+    ux, uy = t[:, 0] / t[:, 2], t[:, 1] / t[:, 2]
+    out_x, out_y = np.abs(ux) > limx, np.abs(uy) > limy
+    assert (out_x & (ux > 0)).any() and (out_x & (ux < 0)).any() and (out_y & (uy > 0)).any() \
+        and (out_y & (uy < 0)).any() and (out_x & out_y).any()
+    edge = sc.subset(np.arange(N))
+    ex = np.clip(ux, -limx, limx) * t[:, 2]
+    ey = np.clip(uy, -limy, limy) * t[:, 2]
+    # float32 rounding keeps the moved means on (not beyond) the edge
+    ex = np.where(np.abs(ex) > limx * t[:, 2], np.nextafter(ex.astype(np.float32), np.float32(0)), ex)
+    ey = np.where(np.abs(ey) > limy * t[:, 2], np.nextafter(ey.astype(np.float32), np.float32(0)), ey)
+    edge.means = np.stack([ex, ey, t[:, 2]], 1).astype(np.float32)
+    Pe = oracle.project(edge, cams, (16, 16))
+    np.testing.assert_allclose(P["cov"][:N], Pe["cov"][:N], rtol=1e-6, atol=1e-9)
+    # projected means: K [R | t] applied to the homogeneous (unmoved) mean
+    K = np.array([[cams.fx[0], 0, cams.cx[0]], [0, cams.fy[0], cams.cy[0]], [0, 0, 1]], np.float64)
+    h = (K @ np.concatenate([cams.viewmat[0].astype(np.float64)], 0) @
+         np.concatenate([sc.means.astype(np.float64), np.ones((N, 1))], 1).T).T
+    np.testing.assert_allclose(P["xy"][:N], h[:, :2] / h[:, 2:], rtol=0, atol=1e-9)
+    assert np.abs(P["xy"][:N, 0] - Pe["xy"][:N, 0])[out_x].min() > 1.0  # the mean itself is not moved
+    # the covariance at the edge is the perspective map's (Monte Carlo)
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(43)
+    for g in np.flatnonzero(out_x | out_y)[:6]:
+        s = np.exp(edge.log_scales[g].astype(np.float64))
+        qq = edge.quats[g].astype(np.float64)
+        Rg = Rotation.from_quat(qq[[1, 2, 3, 0]] / np.linalg.norm(qq)).as_matrix()
+        X = rng.multivariate_normal(edge.means[g].astype(np.float64), Rg @ np.diag(s ** 2) @ Rg.T, size=300_000)
+        u = cams.fx[0] * X[:, 0] / X[:, 2] + cams.cx[0]
+        w = cams.fy[0] * X[:, 1] / X[:, 2] + cams.cy[0]
+        emp = np.cov(np.stack([u, w]))
+        a, b, c = P["cov"][g]
+        model = np.array([[a - 0.3, b], [b, c - 0.3]])
+        assert np.abs(emp - model).max() < 0.03 * np.trace(model), (g, emp, model)
+
+
+def test_backward_through_the_guard_band_matches_central_differences():
+    """Central differences of the whole forward w.r.t. the parameters of
+    Gaussians beyond the guard band (on both sides, on both axes) agree
+    with the oracle's reverse mode, which holds the band's edge fixed in
+    view-angle tangent (so it moves with the depth)."""
+    sc, cams = synth.off_axis_scene(30, 10, sh_degree=1, seed=40)
+    tile, bg = (16, 16), (0.2, 0.1, 0.3)
+    N = sc.n
+    base = oracle.forward(sc, cams, tile, bg=bg)
+    rng = np.random.default_rng(44)
+    w = rng.normal(size=base["img"].shape)
+    grads, g2d, e1 = oracle.backward(sc, cams, base, w, tile, bg)
+    far = np.zeros(N, bool)
+    for v in range(cams.V):
+        t = _camera_space(sc, cams, v)
+        limx, limy = _band(cams, v)
+        # well beyond the edge: no step below moves a Gaussian across it
+        far |= (np.abs(t[:, 0] / t[:, 2]) > 1.05 * limx) | (np.abs(t[:, 1] / t[:, 2]) > 1.05 * limy)
+    contributing = np.intersect1d(np.unique(base["S"][1] % N), np.flatnonzero(far))
+    assert len(contributing) >= 15
+    checked = {}
+    for field in ("means", "log_scales", "quats", "opacity_logits"):
+        arr = getattr(sc, field)
+        checked[field] = 0
+        tries = 0
+        while checked[field] < 10 and tries < 120:
+            tries += 1
+            g = int(rng.choice(contributing))
+            idx = (g,) + tuple(int(rng.integers(0, s)) for s in arr.shape[1:])
+            if field == "means" and checked[field] < 4:
+                idx = (g, 2)  # depth: the band's edge moves with it
+            x0 = float(arr[idx])
+            h = 1e-4 * max(1.0, abs(x0))
+            vals, states, xs = [], [], []
+            for sgn in (1, -1):
+                arr[idx] = np.float32(x0 + sgn * h)
+                xs.append(float(arr[idx]))
+                f = oracle.forward(sc, cams, tile, bg=bg)
+                vals.append(float((w * f["img"]).sum()))
+                states.append((f["chash"].copy(), f["P"]["radius"].copy(), f["P"]["clampmask"].copy()))
+            arr[idx] = np.float32(x0)
+            if not (all(np.array_equal(a, b) for a, b in zip(*states)) and
+                    np.array_equal(states[0][0], base["chash"])):
+                continue
+            fd = (vals[0] - vals[1]) / (xs[0] - xs[1])
+            an = grads[field][idx]
+            assert abs(fd - an) <= 1e-5 * max(1.0, abs(an)) + 1e-6, (field, idx, fd, an)
+            checked[field] += 1
+        assert checked[field] >= 6, checked
+
+
+# ---------------------------------------------------------------------------
+# expected depth (the surface the 3D distance-aware D-SSIM lifts pixels to)
+# ---------------------------------------------------------------------------
+def test_expected_depth_of_one_gaussian_is_depth_times_alpha():
+    f, W, H, z, s = 120.0, 40, 36, 2.5, 0.08
+    cx, cy = float(np.float32(18.3)), float(np.float32(16.6))
+    cams = _cams(W, H, f, [np.eye(3)], [np.zeros(3)], [np.zeros(3)], cx=cx, cy=cy)
+    for logit in (-0.5, 6.0):  # below and at the 0.99 clamp
+        sc = _one_gaussian([0, 0, z], [math.log(s)] * 3, [1, 0, 0, 0], logit, [0.3, 0.6, 0.9])
+        fw = oracle.forward(sc, cams, (16, 16))
+        o = 1 / (1 + math.exp(-float(sc.opacity_logits[0])))
+        vv = (f * math.exp(float(sc.log_scales[0, 0])) / z) ** 2 + 0.3
+        r = math.ceil(3 * math.sqrt(vv + math.sqrt(0.1)))
+        ys, xs = np.mgrid[0:H, 0:W]
+        dx, dy = xs + 0.5 - cx, ys + 0.5 - cy
+        alpha = np.minimum(0.99, o * np.exp(-(dx * dx + dy * dy) / (2 * vv)))
+        alpha = np.where((np.abs(dx) <= r) & (np.abs(dy) <= r) & (alpha >= 1 / 255), alpha, 0.0)
+        np.testing.assert_allclose(fw["depth"].reshape(H, W), z * alpha, rtol=0, atol=1e-12)
+        assert (alpha > 0).sum() > 20
+
+
+def test_expected_depth_weights_each_gaussian_by_its_blend_weight():
+    """Three overlapping Gaussians at three depths with pure red, green and
+    blue colours on black: the colour channels are the blend weights
+    alpha_i T_i (Eq. 1), so the expected depth is sum_i z_i C_i; with all
+    at one depth, D / (1 - T_final) is that depth."""
+    f, W, H = 80.0, 32, 32
+    cams = _cams(W, H, f, [np.eye(3)], [np.zeros(3)], [np.zeros(3)])
+    rgb = np.eye(3)
+    for depths in ((1.5, 2.0, 2.6), (2.2, 2.2, 2.2)):
+        means = [[0.05 * (i - 1) * z, 0.03 * (1 - i) * z, z] for i, z in enumerate(depths)]
+        sh = ((rgb - 0.5) / (0.5 / math.sqrt(math.pi)))[:, None, :].astype(np.float32)
+        sc = synth.Scene(np.asarray(means, np.float32), np.full((3, 3), math.log(0.12), np.float32),
+                         np.tile(np.float32([1, 0, 0, 0]), (3, 1)), np.float32([0.5, 1.0, 2.0]), sh, 0)
+        fw = oracle.forward(sc, cams, (16, 16))
+        C = fw["img"].reshape(3, H * W)
+        z32 = sc.means[:, 2].astype(np.float64)
+        # the colours are 1 and 0 up to the float32 rounding of the SH coefficient
+        np.testing.assert_allclose(fw["P"]["rgb"], rgb, atol=1e-7)
+        np.testing.assert_allclose(fw["depth"], (z32[:, None] * C).sum(0), rtol=1e-6, atol=1e-12)
+        covered = (1 - fw["T"]) > 1e-3
+        assert covered.sum() > 50 and (C > 1e-3).sum(1).min() > 20
+        if len(set(depths)) == 1:
+            np.testing.assert_allclose(fw["depth"][covered] / (1 - fw["T"][covered]), z32[0], rtol=1e-12)
+        else:
+            assert np.abs(fw["depth"][covered] / (1 - fw["T"][covered]) - z32[0]).max() > 0.1
