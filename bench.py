@@ -6,6 +6,11 @@ binning and sort, front-to-back blending, 0.8 L1 + 0.2 D-SSIM loss and its
 gradient, back-to-front blend backward, reduction of the gradients across
 views onto the 3D Gaussians, and the multi-view densification statistics.
 
+The headline workload is 3M SH-3 Gaussians seen by 8 views of mixed
+resolutions (800x600 to 1920x1080) in one persistent launch per stage, with
+the autotuned tile; `secondary_workload` repeats the batched step and the
+per-view loop on 500k Gaussians and 4 views of 1264x832.
+
 Prints one JSON line.  `value` is views per second of the batched path
 (inputs resident in HBM), `e2e` the same through the C ABI with the scene and
 the targets copied from pinned host memory and the loss copied back every
@@ -30,7 +35,8 @@ if ROOT not in sys.path:
 
 import synth  # noqa: E402
 
-WORKLOAD = "multiview_500k_4x1264x832"
+WORKLOAD = "uneven_3m_8views"
+SECONDARY_WORKLOAD = "multiview_500k_4x1264x832"
 LAMBDA = 0.2
 METRIC = "fwd+bwd views/s (batched multi-view vs per-view loop) at oracle tol; serve p50/p99"
 FP32_LANES_PER_SM = 128
@@ -63,6 +69,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph measurements")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrivals per second")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the secondary workload (500k Gaussians, 4 views of 1264x832)")
     ap.add_argument("--no-partial", action="store_true",
                     help="skip the partial-rendering comparison (full / masked / thread-efficient)")
     return ap.parse_args()
@@ -145,7 +153,21 @@ def run_ours(args, rank, world):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     scene, cams, extra = synth.workload(args.workload)
+    sharder = None
+    if world > 1:
+        # weak scaling: a global batch of world x V views (the workload's
+        # resolutions again, new poses; its first V views are the workload's
+        # own), split between the ranks by pixels; one all-reduce per step
+        res = [(int(w), int(h)) for w, h in zip(cams.width, cams.height)] * world
+        cams_g = synth.make_cameras(res, radius=4.0)
+        sharder = shard.ViewShardedStep(rank, world)
+        own, grad_scale = sharder.views([int(p) for p in cams_g.pixels()])
+        cams = cams_g.subset(own)
     V, n = cams.V, scene.n
+    V_total = V if sharder is None else cams_g.V  # views of all ranks per step
+    if sharder is not None:
+        # the other legs measure single-GPU paths: at N > 1 only the sharded step runs
+        args.no_graph = args.no_loop = args.no_partial = args.no_serve = args.no_secondary = True
     targets = synth.make_targets(cams)
     hw = np.stack([cams.height, cams.width], 1).astype(np.int32)
     dev = "cuda"
@@ -167,6 +189,7 @@ def run_ours(args, rank, world):
     loss = torch.empty(V, device=dev)
     dimg = torch.empty_like(tgt)
     acc = [torch.zeros(n, device=dev) for _ in range(3)]
+    incr = [torch.zeros(n, device=dev) for _ in range(3)] if sharder else None
     gm2d = None
     e1 = None
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
@@ -179,12 +202,21 @@ def run_ours(args, rank, world):
         if gm2d is None or gm2d.shape[0] < R:
             gm2d = torch.empty(int(R * 1.2) + 16, 2, device=dev)
             e1 = torch.empty(int(R * 1.2) + 16, device=dev)
+        if sharder is None or rast is not rz:
+            rast.backward(scene_c, dimg_, grads, gm2d, e1)
+            mvgs.adc_accumulate(rast.state, n, gm2d, e1, *acc)
+            return
+        # view-sharded step: this rank's share of the batch-mean loss
+        # gradient, this step's statistic increments, one all-reduce of the
+        # bucket, then the increments join the running statistics
+        dimg_.mul_(grad_scale)
         rast.backward(scene_c, dimg_, grads, gm2d, e1)
-        mvgs.adc_accumulate(rast.state, n, gm2d, e1, *acc)
-        if dist:
-            # data parallel over ranks: each renders its own batch of views
-            # against a replica; gradients and ADC statistics are summed
-            shard.reduce_step(grads, acc)
+        for t_ in incr:
+            t_.zero_()
+        mvgs.adc_accumulate(rast.state, n, gm2d, e1, *incr)
+        sharder.exchange(grads, incr, loss_.sum().reshape(1))
+        for a_, d_ in zip(acc, incr):
+            a_.add_(d_)
 
     def timed(fn, steps, warmup, profile=False):
         for _ in range(warmup):
@@ -274,7 +306,7 @@ def run_ours(args, rank, world):
         rzg.reserve(n, needed[0], needed[1])
         g_b, fits_b = graphed([rzg], [tgt], [hw], [loss], [dimg], [dssim_ws], [rzg.cap.records])
         ms_graph, _ = timed(lambda: g_b.replay(), args.steps, args.warmup)
-        graph = {"views_per_s": V * world / (ms_graph / 1e3), "ms_per_step": ms_graph, "counts_fit": fits_b(),
+        graph = {"views_per_s": V / (ms_graph / 1e3), "ms_per_step": ms_graph, "counts_fit": fits_b(),
                  "launches_per_step": None}
         del g_b
 
@@ -417,6 +449,11 @@ def run_ours(args, rank, world):
                     "densify_note": "includes one count read-back and the allocation of the outputs"}
         del m_st, v_st, p_copy, new_p
 
+    # ---- the secondary workload: batched step and per-view loop ----
+    secondary = None
+    if not args.no_secondary and args.workload != SECONDARY_WORKLOAD:
+        secondary = run_secondary(args, torch, mvgs, timed)
+
     # ---- serving loop: resident 2M SH-3 scene, Poisson arrivals ----
     serving = None
     if not args.no_serve and rank == 0:
@@ -441,7 +478,7 @@ def run_ours(args, rank, world):
     roof, per_stage = roofline(stages, args, needed, rz, clk, V, rz.pixels, blended)
 
     out = {
-        "metric": METRIC, "value": V * world / (ms_batched / 1e3), "unit": "views/s", "n_gpus": world,
+        "metric": METRIC, "value": V_total / (ms_batched / 1e3), "unit": "views/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batched, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "gaussians": n, "sh_degree": scene.sh_degree, "views": V,
@@ -451,9 +488,10 @@ def run_ours(args, rank, world):
                    "autotune_ms": tuning,
                    "records": needed[0], "keys": needed[1],
                    "l2": "512 MB buffer written between timed steps (L2 is 129 MB); per-step working set > 1 GB",
-                   "parallelism": (f"dp{world}: a batch of {V} views per rank, gradient and ADC all-reduce"
+                   "parallelism": (f"dp{world}: a global batch of {V_total} views split between the ranks by "
+                                   "pixels, one all-reduce per step of the gradients and the statistic increments"
                                    if world > 1 else "single")},
-        "e2e": None if ms_e2e is None else {"value": V * world / (ms_e2e / 1e3), "unit": "views/s",
+        "e2e": None if ms_e2e is None else {"value": V_total / (ms_e2e / 1e3), "unit": "views/s",
                                             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "per_view_loop": loop,
@@ -461,6 +499,7 @@ def run_ours(args, rank, world):
         "partial_rendering": partial,
         "training_kernels": training,
         "serving": serving,
+        "secondary_workload": secondary,
         "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in (stages or {}).items() if v[1]},
         "roofline": roof,
         "stage_roofline": per_stage,
@@ -470,6 +509,61 @@ def run_ours(args, rank, world):
         out["cpu_baseline"] = cpu_baseline(args.workload)
     if dist:
         dist.destroy_process_group()
+    return out
+
+
+def run_secondary(args, torch, mvgs, timed):
+    """Views/s of the training step on the 500k-Gaussian, 4 x 1264x832
+    workload (batched, and the per-view launch loop), autotuned tile."""
+    from paper_2506_12727_gb300.autotune import autotune
+    dev = "cuda"
+    scene, cams, _ = synth.workload(SECONDARY_WORKLOAD)
+    V, n = cams.V, scene.n
+    params = {k: torch.tensor(getattr(scene, k), device=dev).contiguous() for k in
+              ("means", "log_scales", "quats", "opacity_logits", "sh")}
+    sc = mvgs.make_scene(params, scene.sh_degree)
+    tile, ppt, _, wb = autotune(sc, cams, params)
+    tgt = torch.tensor(synth.pack_images(synth.make_targets(cams)), device=dev)
+    grads = {k: torch.empty_like(v) for k, v in params.items()}
+    acc = [torch.zeros(n, device=dev) for _ in range(3)]
+
+    def prepare(c, t):
+        h = np.stack([c.height, c.width], 1).astype(np.int32)
+        return dict(rz=mvgs.Rasterizer(c, tile=tile, pixels_per_thread=ppt, smem_batch=wb), tgt=t, hw=h,
+                    loss=torch.empty(c.V, device=dev), dimg=torch.empty_like(t), gm=None, e1=None,
+                    ws=torch.empty(mvgs.dssim_workspace_size(h), dtype=torch.uint8, device=dev))
+
+    def step(d):
+        img = d["rz"].forward(sc)
+        mvgs.dssim_loss(img, d["tgt"], d["hw"], LAMBDA, d["loss"], d["dimg"], d["ws"])
+        R = int(d["rz"].needed.records)
+        if d["gm"] is None or d["gm"].shape[0] < R:
+            d["gm"] = torch.empty(int(R * 1.2) + 16, 2, device=dev)
+            d["e1"] = torch.empty(int(R * 1.2) + 16, device=dev)
+        d["rz"].backward(sc, d["dimg"], grads, d["gm"], d["e1"])
+        mvgs.adc_accumulate(d["rz"].state, n, d["gm"], d["e1"], *acc)
+
+    batch = prepare(cams, tgt)
+    steps = max(10, args.steps // 2)
+    ms_b, _ = timed(lambda: step(batch), steps, max(3, args.warmup))
+    off = synth.view_offsets(cams)
+    singles = [prepare(cams.subset([v]), tgt[off[v]:off[v + 1]].contiguous()) for v in range(V)]
+    acc_grads = {k: torch.zeros_like(v) for k, v in params.items()}
+
+    def loop():
+        for g in acc_grads.values():
+            g.zero_()
+        for d in singles:
+            step(d)
+            for k in acc_grads:
+                acc_grads[k].add_(grads[k])
+    ms_l, _ = timed(loop, steps, 3)
+    out = {"workload": SECONDARY_WORKLOAD, "tile": f"{tile[0]}x{tile[1]}", "pixels_per_thread": ppt or "auto",
+           "smem_batch": wb or "auto", "views_per_s": V / (ms_b / 1e3), "ms_per_step": ms_b,
+           "per_view_loop": {"views_per_s": V / (ms_l / 1e3), "ms_per_step": ms_l,
+                             "speedup_batched_over_loop": ms_l / ms_b}, "steps": steps}
+    del batch, singles, params, grads, acc, acc_grads
+    torch.cuda.empty_cache()
     return out
 
 
@@ -564,12 +658,26 @@ def stage_work(rz, needed, V, pixels, blended):
     }, blended
 
 
-# DRAM bytes (read + write) per blended pair of the blend kernels, from the ncu
-# capture of the benchmark step (profiles/blend_kernels_multiview_500k_
-# 4x1264x832_16x64.md: forward 122.95 MB, backward 216.30 MB per launch over
-# 449,569,394 blended pairs); a launch of another workload is taken in
-# proportion to its blended pairs.  Valid for the kernels as captured.
-DRAM_BYTES_PER_BLENDED = {"blend_forward": 122.95e6 / 449569394, "blend_backward": 216.30e6 / 449569394}
+# DRAM bytes (read + write) per blended pair of the blend kernels, from one
+# ncu capture of the kernels in the headline step, scaled by each launch's
+# blended pairs.  Valid only for the kernel source it was taken on: the
+# capture records a hash of the blend sources, and the line reports no
+# traffic once they differ.
+BLEND_TRAFFIC = {
+    "blend_forward": None,
+    "blend_backward": None,
+    "capture": None,          # profiles/ summary the figures come from
+    "sources_sha256": None,   # of csrc/blend.cu + csrc/common.cuh at capture time
+}
+
+
+def blend_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("blend.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2506_12727_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def roofline(stages, args, needed, rz, clk, V, pixels, blended):
@@ -602,10 +710,13 @@ def roofline(stages, args, needed, rz, clk, V, pixels, blended):
     d.pop("ms")
     d["kernel"] = dom
     d["traffic"] = None
-    if dom in DRAM_BYTES_PER_BLENDED and blended:
-        d["traffic"] = int(DRAM_BYTES_PER_BLENDED[dom] * blended)
-        d["traffic_source"] = ("ncu dram__bytes (read + write) of the kernel in the benchmark step, "
-                               "scaled by blended pairs")
+    if dom in ("blend_forward", "blend_backward") and blended:
+        if BLEND_TRAFFIC[dom] is not None and BLEND_TRAFFIC["sources_sha256"] == blend_sources_hash():
+            d["traffic"] = int(BLEND_TRAFFIC[dom] * blended)
+            d["traffic_source"] = (f"ncu dram__bytes (read + write) per blended pair of the kernel in "
+                                   f"{BLEND_TRAFFIC['capture']}, scaled by this launch's blended pairs")
+        else:
+            d["traffic_source"] = "null: no ncu capture of the current blend sources"
     if d["bound"] == "alu":
         per = FWD_FLOP_PER_BLENDED if dom == "blend_forward" else BWD_FLOP_PER_BLENDED
         d["algorithmic"] = f"{per} FLOP x {blended} blended (pixel, Gaussian) pairs per launch"
@@ -618,101 +729,125 @@ def roofline(stages, args, needed, rz, clk, V, pixels, blended):
 # ---------------------------------------------------------------------------
 # the CPU oracle
 # ---------------------------------------------------------------------------
+ORACLE_TILE = (16, 16)  # the oracle's own binning tile (its images do not depend on it)
 _ORACLE_INPUTS = {}
 
 
-def _oracle_inputs(workload):
-    """The seeded scene, cameras and targets of a workload (generated once
-    per process: generation is not part of a sample)."""
-    if workload not in _ORACLE_INPUTS:
+def _oracle_threads():
+    return max(1, min(64, os.cpu_count() or 1))
+
+
+def _oracle_inputs(workload, threads):
+    """The seeded scene, cameras and targets of a workload, and the scene cut
+    into one contiguous chunk of Gaussians per host thread (generated once per
+    process: generation is not part of a sample)."""
+    key = (workload, threads)
+    if key not in _ORACLE_INPUTS:
         scene, cams, _ = synth.workload(workload)
-        _ORACLE_INPUTS[workload] = (scene, cams, synth.make_targets(cams))
-    return _ORACLE_INPUTS[workload]
+        chunks = np.array_split(np.arange(scene.n), threads)
+        _ORACLE_INPUTS[key] = (scene, cams, synth.make_targets(cams), [(c, scene.subset(c)) for c in chunks])
+    return _ORACLE_INPUTS[key]
 
 
-def oracle_sample(workload, view=0, window=None):
-    """One bounded sample of the workload on the oracle: forward + loss +
-    backward of one view (optionally a pixel window of it).  Returns
-    (seconds, fraction of a full view the sample covers)."""
+def oracle_sample(workload, view=0, window=None, threads=None):
+    """One bounded sample of the workload on the oracle: projection, sort,
+    blend, loss and backward of one view, or of a pixel window of it, with
+    the host threads sharing the work (ctypes releases the GIL while the
+    oracle's C routines run): projection and 3D gradients over chunks of
+    Gaussians, sort, blend and blend backward over row bands of the window,
+    each band with the loss of its own pixels.  Returns (seconds, fraction of
+    a full view covered, threads used)."""
+    import concurrent.futures as cf
     import oracle
-    scene, cams, targets = _oracle_inputs(workload)
+    nt = threads or _oracle_threads()
+    scene, cams, targets, chunks = _oracle_inputs(workload, nt)
     c1 = cams.subset([view])
-    t0 = time.perf_counter()
-    fw = oracle.forward(scene, c1, (16, 16), window=window)
     H, W = int(c1.height[0]), int(c1.width[0])
-    img = fw["img"].reshape(3, H, W)
+    x0, y0, x1, y1 = window if window is not None else (0, 0, W, H)
     tg = targets[view]
-    if window is not None:
-        x0, y0, x1, y1 = window[0]
-        img, tg = img[:, y0:y1, x0:x1], tg[:, y0:y1, x0:x1]
-    _, _, g = oracle.dssim_l1_loss([img], [tg], LAMBDA)
-    d = np.zeros((3, H, W))
-    if window is not None:
-        d[:, y0:y1, x0:x1] = g[0]
-    else:
-        d = g[0]
-    oracle.backward(scene, c1, fw, d.reshape(-1), (16, 16), window=window)
-    dt = time.perf_counter() - t0
-    frac = 1.0 if window is None else ((x1 - x0) * (y1 - y0)) / float(H * W)
-    return dt, frac
-
-
-def _band_sample(args):
-    workload, band = args
-    return oracle_sample(workload, window=np.array([band]))
-
-
-def cpu_baseline(workload):
-    """The oracle on the host: one thread on view 0, and all cores on view 0 cut
-    into one horizontal band per core (spawned processes; each band's loss is
-    the band's own, which moves no work).  The all-cores figure is the main
-    value."""
-    import multiprocessing as mpr
-    dt, frac = oracle_sample(workload)
-    single = {"value": frac / dt, "cores": 1, "seconds": dt,
-              "sample": f"view 0 of {workload}, full resolution, forward + loss + backward, one thread"}
-    _, cams, _ = synth.workload(workload)
-    W, H = int(cams.width[0]), int(cams.height[0])
-    cores = max(1, min(os.cpu_count() or 1, H // 16))
-    bands = [[0, H * i // cores, W, H * (i + 1) // cores] for i in range(cores)]
     t0 = time.perf_counter()
-    with mpr.get_context("spawn").Pool(cores) as pool:
-        parts = pool.map(_band_sample, [(workload, b) for b in bands])
-    wall = time.perf_counter() - t0
-    covered = sum(f for _, f in parts)
-    return {"value": covered / wall, "unit": "views/s", "cores": cores, "kind": "oracle",
-            "sample": f"view 0 of {workload} in {cores} row bands, one process per core (spawned), "
-                      "forward + loss + backward; wall time includes the processes' start",
-            "seconds": wall, "single_thread": single}
+    with cf.ThreadPoolExecutor(nt) as ex:
+        parts = list(ex.map(lambda c: oracle.project(c[1], c1, ORACLE_TILE), chunks))
+        P = {k: np.concatenate([p[k] for p in parts]) for k in parts[0] if isinstance(parts[0][k], np.ndarray)}
+        P["N"], P["V"], P["tile"] = scene.n, 1, ORACLE_TILE
+        rows = np.array_split(np.arange(y0, y1), max(1, min(nt, (y1 - y0) // 16)))
+
+        def band(r):
+            win = np.array([[x0, int(r[0]), x1, int(r[-1]) + 1]], np.int32)
+            S = oracle.sort_keys(c1, ORACLE_TILE, P["valid"], P["rect"], P["depth"].astype(np.float32), win)
+            img, _, _, _ = oracle.render(c1, P, S, (0.0, 0.0, 0.0), win)
+            ya, yb = int(r[0]), int(r[-1]) + 1
+            sub = img.reshape(3, H, W)[:, ya:yb, x0:x1]
+            _, _, g = oracle.dssim_l1_loss([sub], [tg[:, ya:yb, x0:x1]], LAMBDA)
+            d = np.zeros((3, H, W))
+            d[:, ya:yb, x0:x1] = g[0]
+            g2d, _ = oracle.render_backward(c1, P, S, d.reshape(-1), (0.0, 0.0, 0.0), win)
+            return g2d
+        g2d = None
+        for part in ex.map(band, rows):
+            g2d = part if g2d is None else g2d + part
+        list(ex.map(lambda c: oracle.project_backward(c[1], c1, ORACLE_TILE, g2d[c[0]]), chunks))
+    dt = time.perf_counter() - t0
+    return dt, ((x1 - x0) * (y1 - y0)) / float(H * W), nt
+
+
+def cpu_baseline(workload, views=2):
+    """The oracle on the host's cores over the first `views` views of the
+    workload at full resolution (forward + loss + backward of each)."""
+    _, cams, _, _ = _oracle_inputs(workload, _oracle_threads())
+    views = min(views, cams.V)
+    secs, frac, nt = 0.0, 0.0, 1
+    for v in range(views):
+        dt, f, nt = oracle_sample(workload, view=v)
+        secs += dt
+        frac += f
+    return {"value": frac / secs, "unit": "views/s", "cores": nt, "kind": "oracle",
+            "sample": f"views 0-{views - 1} of {workload} at full resolution (the first {views} of the batch), "
+                      f"forward + loss + backward, {nt} host threads (projection and 3D gradients by chunks of "
+                      "Gaussians, blend and its backward by row bands with each band's own loss)",
+            "seconds": secs}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    scene, cams, _ = _oracle_inputs(args.workload)
-    W, H = int(cams.width[0]), int(cams.height[0])
-    # each step is one window of view 0, sized so that the whole run stays
-    # within about two and a half minutes of one core (a 256x256 window takes
-    # ~3.3 s, 128x128 ~1.4 s, 64x64 ~0.8 s on the benchmark scene)
+    nt = _oracle_threads()
+    scene, cams, _, _ = _oracle_inputs(args.workload, nt)
+    # each step is one square window at the centre of one view (views in
+    # turn), sized so that the whole run stays within about two and a half
+    # minutes: the projection and 3D gradients of the whole scene are a
+    # fixed cost per step, the window's pixels the rest
+    t_fixed, _, _ = oracle_sample(args.workload, view=0, window=(0, 0, 8, 8))
+    t_64, _, _ = oracle_sample(args.workload, view=0, window=(0, 0, 64, 64))
+    per_px = max(t_64 - t_fixed, 1e-3) / 4096.0
     per_step = 150.0 / max(1, args.steps + args.warmup)
-    side = 256 if per_step >= 3.5 else (128 if per_step >= 1.5 else 64)
-    side = min(side, W, H)
-    win = np.array([[W // 2 - side // 2, H // 2 - side // 2, W // 2 + side // 2, H // 2 + side // 2]])
-    for _ in range(args.warmup):
-        oracle_sample(args.workload, window=win)
-    times = []
-    frac = None
-    for _ in range(args.steps):
-        dt, frac = oracle_sample(args.workload, window=win)
+    side = 32
+    for s in (512, 384, 256, 192, 128, 96, 64, 48):
+        if t_fixed + s * s * per_px <= per_step:
+            side = s
+            break
+
+    def win(v):
+        W, H = int(cams.width[v]), int(cams.height[v])
+        sd = min(side, W, H)
+        return (W // 2 - sd // 2, H // 2 - sd // 2, W // 2 - sd // 2 + sd, H // 2 - sd // 2 + sd)
+    for i in range(args.warmup):
+        oracle_sample(args.workload, view=i % cams.V, window=win(i % cams.V))
+    times, fracs = [], []
+    for i in range(args.steps):
+        dt, frac, _ = oracle_sample(args.workload, view=i % cams.V, window=win(i % cams.V))
         times.append(dt)
+        fracs.append(frac)
     ms = 1e3 * sum(times) / len(times)
-    value = frac / (ms / 1e3)
-    sample = f"{side}x{side} window at the centre of view 0 of {args.workload}, forward + loss + backward, one thread"
+    value = sum(fracs) / sum(times)
+    sample = (f"a {side}x{side} window at the centre of one view of {args.workload} per step (views in turn), "
+              f"forward + loss + backward, {nt} host threads")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "gaussians": scene.n, "views": cams.V, "tile": "16x16"},
-            "cpu_baseline": {"value": value, "unit": "views/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": args.workload, "gaussians": scene.n, "views": cams.V,
+                       "tile": f"{ORACLE_TILE[0]}x{ORACLE_TILE[1]}"},
+            "cpu_baseline": {"value": value, "unit": "views/s", "cores": nt, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "views/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
