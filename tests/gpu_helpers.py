@@ -75,3 +75,57 @@ def assert_close_rows(got, ref, rtol, atol, what, max_bad=0):
         i = np.unravel_index(np.argmax(err - lim), err.shape)
         raise AssertionError(f"{what}: {nb} of {err.size} entries outside tolerance (rtol={rtol} of the row norm, "
                              f"atol={atol}); worst at {i}: got {g2[i]!r} ref {r2[i]!r}")
+
+
+# ---------------------------------------------------------------------------
+# the oracle on large workloads: its C routines hold no global state and
+# ctypes releases the GIL while they run, so independent views (projection,
+# 3D gradients) and independent pixels (brute force) run on host threads
+# ---------------------------------------------------------------------------
+def _threads():
+    import os
+    return max(1, min(32, os.cpu_count() or 1))
+
+
+def oracle_project(scene, cams, tile):
+    """oracle.project, one view per host thread (same dense [V*N] layout)."""
+    import concurrent.futures
+    import oracle
+    with concurrent.futures.ThreadPoolExecutor(min(_threads(), cams.V)) as ex:
+        parts = list(ex.map(lambda v: oracle.project(scene, cams.subset([v]), tile), range(cams.V)))
+    out = {k: np.concatenate([p[k] for p in parts]) for k in parts[0] if isinstance(parts[0][k], np.ndarray)}
+    out["N"], out["V"], out["tile"] = scene.n, cams.V, tuple(tile)
+    return out
+
+
+def oracle_bruteforce(cams, P, pix, bg=(0.0, 0.0, 0.0)):
+    """oracle.render_pixels_bruteforce over chunks of pixels on host threads."""
+    import concurrent.futures
+    import oracle
+    chunks = np.array_split(np.asarray(pix), _threads())
+    with concurrent.futures.ThreadPoolExecutor(len(chunks)) as ex:
+        parts = list(ex.map(lambda c: oracle.render_pixels_bruteforce(cams, P, c, bg=bg), chunks))
+    return tuple(np.concatenate([p[i] for p in parts]) for i in range(4))
+
+
+def oracle_window_forward_backward(scene, cams, tile, win, dimg_fn, bg=(0.0, 0.0, 0.0)):
+    """oracle.forward + oracle.backward restricted to a pixel window per view,
+    with the projection and the 3D gradients (summed over views) computed
+    one view per thread.  `dimg_fn(ref)` returns dL/dimage (packed) from the
+    forward's outputs.  Returns (ref, dimg, grads, g2d)."""
+    import concurrent.futures
+    import oracle
+    P = oracle_project(scene, cams, tile)
+    S = oracle.sort_keys(cams, tile, P["valid"], P["rect"], P["depth"].astype(np.float32), win)
+    img, T, last, amb, chash, depth = oracle.render(cams, P, S, bg, win, want_hash=True)
+    ref = dict(P=P, S=S, img=img, T=T, last=last, amb=amb, chash=chash, depth=depth)
+    dimg = dimg_fn(ref)
+    g2d, e1 = oracle.render_backward(cams, P, S, dimg.astype(np.float64), bg, win)
+    N = scene.n
+
+    def one(v):
+        return oracle.project_backward(scene, cams.subset([v]), tile, g2d[v * N:(v + 1) * N])
+    with concurrent.futures.ThreadPoolExecutor(min(_threads(), cams.V)) as ex:
+        parts = list(ex.map(one, range(cams.V)))
+    grads = {k: sum(p[k] for p in parts) for k in parts[0]}
+    return ref, dimg, grads, g2d

@@ -45,6 +45,10 @@ def _small_cases():
         "single_view_10k_sh0": (synth.make_scene(10_000, 0), synth.make_cameras([(128, 128)], radius=3.0)),
         "multiview_sh3_ragged": (synth.make_scene(6_000, 3, seed=5),
                                  synth.make_cameras([(150, 97), (64, 130), (201, 45)], radius=4.0, seed=6)),
+        # half of the Gaussians beyond the guard band of the projection
+        # Jacobian (1.4-1.9x the half-FOV tangent), large enough to reach
+        # into the image: records whose covariance uses the clamped J
+        "off_axis_guard_band_sh3": synth.off_axis_scene(300, 300, sh_degree=3, W=96, H=72, seed=45),
     }
 
 
