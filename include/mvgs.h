@@ -408,7 +408,8 @@ mvgs_status mvgs_dssim_loss(const float* img, const float* target, const int32_t
  * holds it until exit), enough for about 2.2 million pixels per call (one
  * 1920x1080 view); larger calls return MVGS_ENOSPACE without launching.  The
  * first call on a device looks up the array's address on that device (make
- * that call before any stream capture).  Calls share the array, so calls
+ * that call before any stream capture) and keeps it for the life of the
+ * process (not valid after cudaDeviceReset).  Calls share the array, so calls
  * that overlap on the GPU race; nothing in it needs clearing between calls. */
 mvgs_status mvgs_dssim_loss_noalloc(const float* img, const float* target, const int32_t* hw, int32_t V,
                                     float lambda, float* loss_per_view, float* dL_dimg, mvgs_stream stream);

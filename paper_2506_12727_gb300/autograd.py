@@ -7,7 +7,9 @@ blend state between the two is what the forward keeps in the rasterizer's
 state buffer (sorted lists, final transmittance, last contributor per pixel);
 the backward recomputes each pixel's transmittances from it instead of
 storing per-pixel lists.  One rasterizer holds one forward's state: call its
-backward before the next forward on the same rasterizer.
+backward before the next forward on the same rasterizer (a backward whose
+state a later forward has overwritten raises instead of returning wrong
+gradients).
 
 Optional per-record outputs for the densification statistics can be requested
 with `adc=(g_mean2d, e1)` buffers (see mvgs_render_views_backward).
@@ -28,6 +30,7 @@ class _RenderViews(torch.autograd.Function):
         params = dict(zip(PARAMS, tensors))
         img = rasterizer.forward(mvgs.make_scene(params, sh_degree))
         ctx.rasterizer = rasterizer
+        ctx.generation = rasterizer.generation
         ctx.sh_degree = sh_degree
         ctx.adc = adc
         ctx.save_for_backward(*tensors)
@@ -35,6 +38,9 @@ class _RenderViews(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, dimg):
+        if ctx.rasterizer.generation != ctx.generation:
+            raise RuntimeError("the rasterizer's state belongs to a later forward: call backward before rendering "
+                               "again with the same rasterizer, or use one rasterizer per pending backward")
         tensors = ctx.saved_tensors
         params = dict(zip(PARAMS, tensors))
         grads = {k: torch.empty_like(v) for k, v in params.items()}

@@ -12,8 +12,10 @@
 // The array is static device storage: every GPU that loads the library holds
 // kScratchBytes of it until the process exits.  Its device address is looked
 // up once per device (the first call on that device, with that device
-// current) and cached; that first call should therefore come before any
-// stream capture.  All calls share the array and it keeps the previous call's
+// current) and cached for the life of the process; that first call should
+// therefore come before any stream capture, and, like every device pointer
+// taken before it, the cached address is not valid after cudaDeviceReset
+// (do not call this entry point after resetting the device).  All calls share the array and it keeps the previous call's
 // contents; the loss kernels write every scratch value before reading it, so
 // nothing needs clearing, but calls that overlap on the GPU (different
 // streams, no ordering between them) race on the array.

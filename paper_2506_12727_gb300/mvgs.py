@@ -440,6 +440,9 @@ class Rasterizer:
         self.n = None
         self.pixels = int(sum(int(w) * int(h) for w, h in zip(cams.width, cams.height)))
         self.needed = Capacity(0, 0)
+        # forwards run so far: a backward that needs one forward's state can
+        # check that no later forward has overwritten it
+        self.generation = 0
 
     def _ensure(self, n, records, keys):
         grow = self.state is None or n != self.n or records > self.cap.records or keys > self.cap.keys
@@ -521,6 +524,7 @@ class Rasterizer:
         n = scene_c.n
         if images is None:
             images = torch.empty(3 * self.pixels, dtype=torch.float32, device=self.device)
+        self.generation += 1
         if self.capturable:
             # no read-backs, no growing: the caller reserved the capacity and
             # checks fits() after the step

@@ -211,3 +211,19 @@ def test_window_gradients_match_oracle(setup):
         # cancels in dense scenes slightly off for a handful of Gaussians per
         # million; more than 1 per million fails
         assert_close_rows(got, exp, 1e-3, 1e-5 * np.abs(exp).max(), "d" + k, max_bad=got.size // 1_000_000)
+
+
+def test_backward_after_a_later_forward_on_the_same_rasterizer_raises(cuda_lib):
+    """One rasterizer holds one forward's state: a backward whose state a
+    second forward overwrote is refused (not silently wrong)."""
+    from paper_2506_12727_gb300 import autograd
+    scene = synth.make_scene(2000, 3, seed=91)
+    cams = synth.make_cameras([(64, 48), (48, 64)], radius=3.0, seed=92)
+    rz = cuda_lib.Rasterizer(cams, tile=(16, 16))
+    ps = {k: v.clone().requires_grad_(True) for k, v in scene_to_device(scene).items()}
+    first = autograd.render(rz, ps, 3)
+    second = autograd.render(rz, ps, 3)
+    with pytest.raises(RuntimeError, match="later forward"):
+        first.sum().backward()
+    second.sum().backward()  # the latest forward's backward still runs
+    assert torch.isfinite(ps["means"].grad).all() and ps["means"].grad.abs().max() > 0
