@@ -585,9 +585,9 @@ def run_serving(args, torch, mvgs):
     pool = synth.poisson_requests(400, rate_hz=args.serve_rate)
     cams = [synth.make_cameras(r["resolutions"], radius=(3.0, 5.0), seed=r["cam_seed"]) for r in pool]
 
-    def server():
+    def server(coalesce_ms=0.0, coalesce_views=0):
         return serve.Server(params, 3, tile=(16, 64), slots=2, max_views=32, max_pixels=40_000_000,
-                            memory_budget=96 << 30)
+                            memory_budget=96 << 30, coalesce_ms=coalesce_ms, coalesce_views=coalesce_views)
 
     out = {"scene": "2M SH-3 resident", "tile": "16x64", "slots": 2,
            "latency": "arrival to completion of the request's batch on the device; images stay on the device"}
@@ -602,19 +602,29 @@ def run_serving(args, torch, mvgs):
                        "requests": len(cap_reqs), "failed": len(cap_reqs) - len(done)}
     srv.close()
     traces = {}
-    for name, rate in (("configured_rate", args.serve_rate), ("at_70pct_capacity", 0.7 * cap_rps)):
+    # (name, offered rate, coalescing window ms, coalescing target views)
+    runs = (("configured_rate", args.serve_rate, 0.0, 0), ("at_70pct_capacity", 0.7 * cap_rps, 0.0, 0),
+            ("at_70pct_capacity_coalesced", 0.7 * cap_rps, 40.0, 24))
+    for name, rate, cms, cviews in runs:
         n = int(min(len(pool) - 30, max(8, cap_rps * 10.0)))  # about 10 s of work
         rng = np.random.default_rng(3)
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
         reqs = [serve.Request(30 + i, cams[30 + i]) for i in range(n)]
-        srv = server()
-        t0 = _time.perf_counter()
+        srv = server(cms, cviews)
         wall = serve.run_trace(srv, reqs, list(arrivals - arrivals[0]), realtime=True, timeout_s=60)
         srv.close()
         st = serve.latency_summary(reqs)
+        log = srv.batch_log
         st.update({"offered_requests_per_s": rate, "wall_s": wall, "views_per_s": st["views"] / wall,
-                   "batches": len(srv.batch_log),
-                   "mean_requests_per_batch": float(np.mean([b[3] for b in srv.batch_log])) if srv.batch_log else 0})
+                   "coalesce_ms": cms, "coalesce_views": cviews, "batches": len(log),
+                   "mean_requests_per_batch": float(np.mean([b[3] for b in log])) if log else 0,
+                   "mean_views_per_batch": float(np.mean([b[1] for b in log])) if log else 0,
+                   # per batch: device time of the render call (CUDA events on the
+                   # worker's stream) and host time from taking the batch to its
+                   # completion (adds the two count read-backs' waits, launches and
+                   # the Python around the call)
+                   "batch_device_ms_mean": float(np.mean([b[4] for b in log])) if log else 0,
+                   "batch_host_ms_mean": float(np.mean([b[5] for b in log])) if log else 0})
         traces[name] = st
     out["traces"] = traces
     main = traces["configured_rate"]

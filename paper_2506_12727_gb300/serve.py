@@ -20,7 +20,12 @@ state/workspace buffers:
     single request that does not fit is rendered a part of its views at a
     time, and fails only if one of its views does not fit alone;
   - a failure inside a batch fails that batch's requests (with the message)
-    and the worker carries on.
+    and the worker carries on;
+  - optionally (`coalesce_ms` > 0) a free worker lets arrivals gather before
+    it takes a batch: it waits until the queue holds `coalesce_views` views
+    or its oldest request has waited `coalesce_ms`, so that at moderate load
+    batches hold several requests instead of one (fewer, fuller launches, at
+    the price of that wait in latency).
 
 Each view is rendered with exactly the arithmetic it would get alone (the
 batch only adds other views' keys to the sort), so a request's images do not
@@ -82,7 +87,8 @@ class Request:
 
 class Server:
     def __init__(self, params: dict, sh_degree: int, tile=(16, 16), bg=(0.0, 0.0, 0.0), slots=2, max_views=32,
-                 max_pixels=48_000_000, memory_budget=64 << 30, pixels_per_thread=0, device="cuda"):
+                 max_pixels=48_000_000, memory_budget=64 << 30, pixels_per_thread=0, device="cuda", coalesce_ms=0.0,
+                 coalesce_views=0):
         self.params = {k: v.contiguous() for k, v in params.items()}
         self.scene_c = mvgs.make_scene(self.params, sh_degree)
         self.tile, self.bg, self.ppt, self.device = tuple(tile), tuple(bg), pixels_per_thread, device
@@ -91,8 +97,11 @@ class Server:
         self.queue: collections.deque[Request] = collections.deque()
         self.cv = threading.Condition()
         self.closing = False
+        self.coalesce_s, self.coalesce_views = coalesce_ms / 1e3, coalesce_views
         self.batches = 0
-        self.batch_log = []  # (batch id, views, pixels, requests, ms on the device)
+        # per batch: (batch id, views, pixels, requests, ms on the device, ms from
+        # taking the batch to its completion on the host clock)
+        self.batch_log = []
         self.workers = [threading.Thread(target=self._worker, args=(i,), daemon=True) for i in range(slots)]
         self._dev_index = torch.device(device).index or 0
         for w in self.workers:
@@ -148,15 +157,23 @@ class Server:
         rz = None
         while True:
             with self.cv:
-                while not self.queue and not self.closing:
-                    self.cv.wait()
-                if not self.queue and self.closing:
-                    return
+                while True:
+                    while not self.queue and not self.closing:
+                        self.cv.wait()
+                    if not self.queue and self.closing:
+                        return
+                    if self.coalesce_s > 0 and not self.closing:
+                        age = time.perf_counter() - self.queue[0].t_arrival
+                        if sum(r.views for r in self.queue) < self.coalesce_views and age < self.coalesce_s:
+                            self.cv.wait(self.coalesce_s - age)
+                            continue
+                    break
                 batch = self._take_batch()
                 bid = self.batches
                 self.batches += 1
+            t_take = time.perf_counter()
             try:
-                rz = self._render(batch, bid, stream, rz)
+                rz = self._render(batch, bid, stream, rz, t_take)
             except Exception as e:  # a failed batch fails its requests, not the server
                 rz = None
                 torch.cuda.empty_cache()
@@ -212,7 +229,7 @@ class Server:
             ms += t
         return torch.cat(parts), ms, rz
 
-    def _render(self, batch, bid, stream, rz):
+    def _render(self, batch, bid, stream, rz, t_take):
         cams = CameraBatch([r.cams for r in batch])
         try:
             img, ms, rz = self._forward(cams, stream, rz)
@@ -223,13 +240,16 @@ class Server:
             if len(batch) == 1:
                 img, ms, rz = self._render_request_in_parts(batch[0], stream, rz)
             else:
-                # split: render the first half now, requeue the rest at the front
+                # split: render the first half now, requeue the rest at the front;
+                # the batch list (the worker's) keeps only the first half, so a
+                # failure from here on fails only the requests this worker holds
                 half = len(batch) // 2
                 with self.cv:
                     for r in reversed(batch[half:]):
                         self.queue.appendleft(r)
+                    del batch[half:]
                     self.cv.notify()
-                return self._render(batch[:half], bid, stream, rz)
+                return self._render(batch, bid, stream, rz, t_take)
         t = time.perf_counter()
         off = 0
         for r in batch:
@@ -241,7 +261,7 @@ class Server:
             r.done.set()
         with self.cv:
             self.batch_log.append((bid, cams.V, int(np.sum(cams.width.astype(np.int64) * cams.height)), len(batch),
-                                   ms))
+                                   ms, (t - t_take) * 1e3))
         return rz
 
 

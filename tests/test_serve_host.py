@@ -120,3 +120,49 @@ def test_only_the_request_whose_view_cannot_fit_fails(serve_mod, monkeypatch):
     for r in (reqs[0], reqs[2]):
         assert r.error is None, r.error
         assert torch.equal(r.images, _expected(r))
+
+
+def test_a_failure_after_a_split_fails_only_the_half_that_failed(serve_mod, monkeypatch):
+    """A batch over the limit is split and its tail requeued; when the first
+    half then fails, the requeued requests are rendered, not failed."""
+    mvgs, serve = serve_mod
+    srv = _server(serve_mod, monkeypatch, limit=2, slots=1, max_views=8)
+    reqs = _requests(serve, [2, 2], special=0)  # request 0 holds a view that never fits
+    with srv.cv:
+        for r in reqs:
+            r.t_arrival = 0.0
+            srv.queue.append(r)
+        srv.cv.notify()
+    for r in reqs:
+        assert r.done.wait(10), r.rid
+    srv.close()
+    assert reqs[0].error is not None and "MemoryBudgetError" in reqs[0].error
+    assert reqs[1].error is None, reqs[1].error
+    assert torch.equal(reqs[1].images, _expected(reqs[1]))
+
+
+def test_coalescing_gathers_arrivals_into_one_batch(serve_mod, monkeypatch):
+    """With a coalescing window a free worker waits for more views (up to the
+    window) before taking a batch: three requests arriving 20 ms apart share
+    one batch; a lone request goes once the window has passed."""
+    import time
+    mvgs, serve = serve_mod
+    srv = _server(serve_mod, monkeypatch, limit=64, slots=1, coalesce_ms=2000.0, coalesce_views=6)
+    reqs = _requests(serve, [2, 2, 2])
+    for r in reqs:
+        srv.submit(r)
+        time.sleep(0.02)
+    for r in reqs:
+        assert r.done.wait(10), r.rid
+    assert len(srv.batch_log) == 1 and srv.batch_log[0][3] == 3
+    for r in reqs:
+        assert torch.equal(r.images, _expected(r))
+    srv.close()
+    srv = _server(serve_mod, monkeypatch, limit=64, slots=1, coalesce_ms=50.0, coalesce_views=100)
+    (r,) = _requests(serve, [1])
+    t0 = time.perf_counter()
+    srv.submit(r)
+    assert r.done.wait(10)
+    waited = time.perf_counter() - t0
+    srv.close()
+    assert r.error is None and 0.04 <= waited < 5.0
