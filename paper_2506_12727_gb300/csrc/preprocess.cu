@@ -281,6 +281,20 @@ __device__ __forceinline__ void for_each_sh(const float* __restrict__ row, bool 
     for (int e = 0; e < E; e++) f(e, __ldg(row + e));
 }
 
+// A thread's SH coefficients staged once in shared memory, in a column of
+// its own (element e of thread t at e * BS + t: consecutive threads hit
+// consecutive banks), so the walk over the Gaussian's views reads them from
+// shared memory instead of re-reading the 48-float row through L1 for every
+// view -- at degree 3 the rows of all resident threads do not fit L1, and the
+// re-reads went to L2 and HBM.  Only the owning thread reads its column: no
+// block barrier is needed.
+template <int NK, int BS>
+__device__ __forceinline__ float* stage_sh(const float* __restrict__ row, bool vec_ok, float* smem) {
+    float* col = smem + threadIdx.x;
+    for_each_sh<NK>(row, vec_ok, [&](int e, float c) { col[e * BS] = c; });
+    return col;
+}
+
 // Participation pre-count for sizing: per Gaussian, the visible views and the
 // tiles they cover (the same projection as the render, so the totals are the
 // render's record and key counts exactly).
@@ -303,8 +317,10 @@ __global__ void __launch_bounds__(256) count_keys_kernel(SceneArgs sc, const Dev
     keys[g] = (uint32_t)(k < 0xffffffffull ? k : 0xffffffffull);
 }
 
+constexpr int PRE_THREADS = 128;
+
 template <int DEG>
-__global__ void __launch_bounds__(256) preprocess_kernel(SceneArgs sc, const DevCam* __restrict__ cams, int V, int tw,
+__global__ void __launch_bounds__(PRE_THREADS) preprocess_kernel(SceneArgs sc, const DevCam* __restrict__ cams, int V, int tw,
                                                          int th, const uint8_t* __restrict__ vis, RecordArgs rec,
                                                          uint32_t* __restrict__ depth_keys,
                                                          uint32_t* __restrict__ rec_ids,
@@ -317,6 +333,8 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneArgs sc, const Dev
     long long r = rec.rec_off[g];
     const float* shg = sc.sh + (size_t)g * NK * 3;
     const bool sh_vec = (reinterpret_cast<uintptr_t>(sc.sh) & 15) == 0;  // rows of 48 floats stay 16-byte aligned
+    __shared__ float s_sh[NK * 3 * PRE_THREADS];
+    const float* shc = stage_sh<NK, PRE_THREADS>(shg, sh_vec, s_sh);
     for (int v = 0; v < V; v++) {
         if (!vis[g * V + v]) continue;
         if (r >= rec.cap) break;  // capturable mode past its record capacity (reported through the counts)
@@ -337,7 +355,8 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneArgs sc, const Dev
         sh_basis<DEG>(dx, dy, dz, Y);
         float rgb[3] = {0.5f, 0.5f, 0.5f};
         int clamp = 0;
-        for_each_sh<NK>(shg, sh_vec, [&](int e, float c) { rgb[e % 3] += Y[e / 3] * c; });
+#pragma unroll
+        for (int e = 0; e < NK * 3; e++) rgb[e % 3] += Y[e / 3] * shc[e * PRE_THREADS];
 #pragma unroll
         for (int ch = 0; ch < 3; ch++) {
             if (rgb[ch] < 0.f) { clamp |= 1 << ch; rgb[ch] = 0.f; }
@@ -380,6 +399,8 @@ __global__ void __launch_bounds__(128, 3) preprocess_backward_kernel(SceneArgs s
     load_gauss(sc, g, G, true);
     const float* shg = sc.sh + (size_t)g * NK * 3;
     const bool sh_vec = (reinterpret_cast<uintptr_t>(sc.sh) & 15) == 0;  // rows of 48 floats stay 16-byte aligned
+    __shared__ float s_sh[NK * 3 * 128];
+    const float* shc = stage_sh<NK, 128>(shg, sh_vec, s_sh);
     float gmu[3] = {0.f, 0.f, 0.f};
     float gS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma, symmetric (xx, xy, xz, yy, yz, zz)
     float go = 0.f;
@@ -477,7 +498,8 @@ __global__ void __launch_bounds__(128, 3) preprocess_backward_kernel(SceneArgs s
 #pragma unroll
             for (int ch = 0; ch < 3; ch++) gsh[3 * k + ch] += Y[k] * grgb[ch];
         }
-        for_each_sh<NK>(shg, sh_vec, [&](int e, float c) { wk[e / 3] += c * grgb[e % 3]; });
+#pragma unroll
+        for (int e = 0; e < NK * 3; e++) wk[e / 3] += shc[e * 128] * grgb[e % 3];
         const float3 gd = sh_basis_grad<DEG>(dx, dy, dz, wk);
         const float dd = gd.x * dx + gd.y * dy + gd.z * dz;
         gmu[0] += (gd.x - dx * dd) * il;
@@ -585,9 +607,9 @@ void launch_preprocess(const SceneArgs& sc, const DevCam* cams, int V, int tw, i
                        const RecordArgs& rec, uint32_t* depth_keys, uint32_t* rec_ids, uint32_t* tiles_touched,
                        cudaStream_t s) {
     if (sc.n == 0) return;
-    const unsigned nb = blocks_for(sc.n, 256);
+    const unsigned nb = blocks_for(sc.n, PRE_THREADS);
 #define MVGS_PP(D) \
-    preprocess_kernel<D><<<nb, 256, 0, s>>>(sc, cams, V, tw, th, vis, rec, depth_keys, rec_ids, tiles_touched)
+    preprocess_kernel<D><<<nb, PRE_THREADS, 0, s>>>(sc, cams, V, tw, th, vis, rec, depth_keys, rec_ids, tiles_touched)
     switch (sc.sh_degree) {
         case 0: MVGS_PP(0); break;
         case 1: MVGS_PP(1); break;
