@@ -506,26 +506,29 @@ static mvgs_status render_impl(const mvgs_scene* scene, const mvgs_camera* cams,
     const Count Rc = capt ? Count((unsigned long long)cap->records, dcnt) : Count((unsigned long long)R);
 
     // projection, colour, radius and tile rectangle of every record
-    uint32_t* dkeys_a = at<uint32_t>(workspace, P.w_dkeys_a);
-    uint32_t* ids_a = at<uint32_t>(workspace, P.w_ids_a);
     uint32_t* tiles = at<uint32_t>(workspace, P.w_tiles);
     {
         StageTimer t(MVGS_STAGE_PREPROCESS, s);
-        launch_preprocess(sc, dcams, V, tw, th, at<uint8_t>(workspace, P.w_vis), rec, dkeys_a, ids_a, tiles, s);
+        launch_preprocess(sc, dcams, V, tw, th, at<uint8_t>(workspace, P.w_vis), rec, tiles, s);
     }
 
-    // records by depth, then keys per covered tile in that order
+    // records by depth (the keys are the records' float32 depths, positive, so
+    // their bits sort as unsigned integers; the values the record indices),
+    // with each record's tile count carried into depth order by the last pass;
+    // then keys per covered tile in that order
     uint32_t* order = at<uint32_t>(workspace, P.w_order);
+    uint32_t* tiles_by_depth = at<uint32_t>(workspace, P.w_ids_a);
     {
         StageTimer t(MVGS_STAGE_DEPTH_SORT, s);
-        radix_sort_pairs(dkeys_a, ids_a, at<uint32_t>(workspace, P.w_dkeys_b), at<uint32_t>(workspace, P.w_ids_b),
-                         order, Rc, 32, at<void>(workspace, P.w_radix), s);
+        radix_sort_pairs(reinterpret_cast<const uint32_t*>(rec.depth), nullptr, at<uint32_t>(workspace, P.w_dkeys_a),
+                         tiles_by_depth, at<uint32_t>(workspace, P.w_dkeys_b), at<uint32_t>(workspace, P.w_ids_b),
+                         order, Rc, 32, at<void>(workspace, P.w_radix), s, tiles, tiles_by_depth);
     }
     unsigned long long* tile_off = at<unsigned long long>(workspace, P.w_tile_off);
     {
         StageTimer t(MVGS_STAGE_SCAN_TILES, s);
-        scan_gather_u32_to_u64(tiles, order, tile_off, Rc, capt ? dcnt + 1 : nullptr, at<void>(workspace, P.w_scan),
-                               s);
+        scan_u32_to_u64_count(tiles_by_depth, tile_off, Rc, capt ? dcnt + 1 : nullptr, at<void>(workspace, P.w_scan),
+                              s);
     }
     unsigned long long K = 0;
     if (!capt) {

@@ -52,7 +52,7 @@ void launch_count_visible(const SceneArgs& sc, const DevCam* cams, int V, int tw
 // bits of the depth), the identity permutation, and the number of tiles each
 // record touches.
 void launch_preprocess(const SceneArgs& sc, const DevCam* cams, int V, int tw, int th, const uint8_t* vis,
-                       const RecordArgs& rec, uint32_t* depth_keys, uint32_t* rec_ids, uint32_t* tiles_touched,
+                       const RecordArgs& rec, uint32_t* tiles_touched,
                        cudaStream_t s);
 void launch_zero_f32(float* p, size_t count, cudaStream_t s);
 // rec_grad: [records, kGradStride] float (mean2d, -, -, -, opacity, rgb, e1 at
@@ -74,16 +74,21 @@ void scan_masked_i32_to_i64(const int* in, int mask, long long* out, uint64_t n,
 void scan_u32_to_u64(const uint32_t* in, unsigned long long* out, uint64_t n, void* tmp, cudaStream_t s);
 // gathered variant: scans in[idx[i]]
 // (also the total into *total when given; n may be a device count)
+void scan_u32_to_u64_count(const uint32_t* in, unsigned long long* out, Count n, unsigned long long* total,
+                           void* tmp, cudaStream_t s);
 void scan_gather_u32_to_u64(const uint32_t* in, const uint32_t* idx, unsigned long long* out, Count n,
                             unsigned long long* total, void* tmp, cudaStream_t s);
 
 size_t radix_temp_bytes(uint64_t n);
 size_t tile_sort_temp_bytes(uint64_t K);
 // Stable LSD sort of (key, value) pairs on key bits [0, bits).  Input in
-// (keys_a, vals_a), which are overwritten; buffers _b are scratch; the sorted
-// values end in vals_out.
-void radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b, uint32_t* vals_out,
-                      Count n, int bits, void* tmp, cudaStream_t s);
+// (keys0, vals0), read only; vals0 == nullptr sorts the identity permutation
+// (values generated, not read).  keys_a/b and vals_a/b are scratch; the sorted
+// values end in vals_out.  With gather_src, the last pass also writes
+// gather_out[i] = gather_src[vals_out[i]] (gather_out may be vals_a).
+void radix_sort_pairs(const uint32_t* keys0, const uint32_t* vals0, uint32_t* keys_a, uint32_t* vals_a,
+                      uint32_t* keys_b, uint32_t* vals_b, uint32_t* vals_out, Count n, int bits, void* tmp,
+                      cudaStream_t s, const uint32_t* gather_src = nullptr, uint32_t* gather_out = nullptr);
 
 // Stable sort, by global (view, tile) id, of one entry per (record, covered
 // tile) taken in the order of `order` (records sorted by depth); tile_off is

@@ -322,8 +322,6 @@ constexpr int PRE_THREADS = 128;
 template <int DEG>
 __global__ void __launch_bounds__(PRE_THREADS) preprocess_kernel(SceneArgs sc, const DevCam* __restrict__ cams, int V, int tw,
                                                          int th, const uint8_t* __restrict__ vis, RecordArgs rec,
-                                                         uint32_t* __restrict__ depth_keys,
-                                                         uint32_t* __restrict__ rec_ids,
                                                          uint32_t* __restrict__ tiles_touched) {
     constexpr int NK = (DEG + 1) * (DEG + 1);
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -365,8 +363,6 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_kernel(SceneArgs sc, c
         rec.clamp[r] = clamp;
         rec.depth[r] = P.depth;
         rec.rect[r] = P.rect;
-        depth_keys[r] = __float_as_uint(P.depth);
-        rec_ids[r] = (uint32_t)r;
         tiles_touched[r] = (uint32_t)((P.rect.z - P.rect.x) * (P.rect.w - P.rect.y));
         r++;
     }
@@ -604,12 +600,12 @@ void launch_count_visible(const SceneArgs& sc, const DevCam* cams, int V, int tw
 }
 
 void launch_preprocess(const SceneArgs& sc, const DevCam* cams, int V, int tw, int th, const uint8_t* vis,
-                       const RecordArgs& rec, uint32_t* depth_keys, uint32_t* rec_ids, uint32_t* tiles_touched,
+                       const RecordArgs& rec, uint32_t* tiles_touched,
                        cudaStream_t s) {
     if (sc.n == 0) return;
     const unsigned nb = blocks_for(sc.n, PRE_THREADS);
 #define MVGS_PP(D) \
-    preprocess_kernel<D><<<nb, PRE_THREADS, 0, s>>>(sc, cams, V, tw, th, vis, rec, depth_keys, rec_ids, tiles_touched)
+    preprocess_kernel<D><<<nb, PRE_THREADS, 0, s>>>(sc, cams, V, tw, th, vis, rec, tiles_touched)
     switch (sc.sh_degree) {
         case 0: MVGS_PP(0); break;
         case 1: MVGS_PP(1); break;

@@ -191,7 +191,8 @@ template <bool WRITE_KEYS, class GetVal>
 __device__ __forceinline__ void rank_and_scatter(RankSmem& sm, const uint32_t (&k)[RS_ITEMS], uint64_t n, int shift,
                                                  const uint32_t* __restrict__ offsets, uint32_t nblocks,
                                                  uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                                 GetVal get_val) {
+                                                 GetVal get_val, const uint32_t* __restrict__ gsrc = nullptr,
+                                                 uint32_t* __restrict__ gout = nullptr) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const uint64_t block0 = (uint64_t)blockIdx.x * RS_TILE;
@@ -253,6 +254,7 @@ __device__ __forceinline__ void rank_and_scatter(RankSmem& sm, const uint32_t (&
         const uint32_t pos = sm.boff[d] + (uint32_t)i - sm.dstart[d];
         vout[pos] = sm.svals[i];
         if (WRITE_KEYS) kout[pos] = key;
+        if (gout) gout[pos] = gsrc[sm.svals[i]];
     }
 }
 
@@ -278,12 +280,17 @@ __global__ void __launch_bounds__(RS_THREADS) rs_upsweep(const uint32_t* __restr
     counts[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = sum;
 }
 
+// vin == nullptr: the values are the keys' positions (an identity
+// permutation, generated instead of read).  gout != nullptr: also writes
+// gout[pos] = gsrc[value] (a per-element array carried into sorted order).
 template <bool WRITE_KEYS>
-__global__ void __launch_bounds__(RS_THREADS, 2) rs_downsweep(const uint32_t* __restrict__ kin,
+__global__ void __launch_bounds__(RS_THREADS, 3) rs_downsweep(const uint32_t* __restrict__ kin,
                                                              const uint32_t* __restrict__ vin,
                                                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                              Count cn, int shift,
-                                                             const uint32_t* __restrict__ offsets, uint32_t nblocks) {
+                                                             const uint32_t* __restrict__ offsets, uint32_t nblocks,
+                                                             const uint32_t* __restrict__ gsrc = nullptr,
+                                                             uint32_t* __restrict__ gout = nullptr) {
     __shared__ RankSmem sm;
     const uint64_t n = cn.get();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -296,8 +303,9 @@ __global__ void __launch_bounds__(RS_THREADS, 2) rs_downsweep(const uint32_t* __
         const uint64_t idx = base + (uint64_t)j * 32;
         k[j] = idx < n ? kin[idx] : 0u;
     }
-    rank_and_scatter<WRITE_KEYS>(sm, k, n, shift, offsets, nblocks, kout, vout,
-                                 [&](int local) { return vin[block0 + local]; });
+    rank_and_scatter<WRITE_KEYS>(
+        sm, k, n, shift, offsets, nblocks, kout, vout,
+        [&](int local) { return vin ? vin[block0 + local] : (uint32_t)(block0 + local); }, gsrc, gout);
 }
 
 // ---------------------------------------------------------------------------
@@ -359,7 +367,7 @@ __global__ void block_starts_kernel(const unsigned long long* __restrict__ off, 
     for (uint64_t b = b0; b < b1 && b < nblocks; b++) first[b] = (uint32_t)r;
 }
 
-__global__ void __launch_bounds__(RS_THREADS) dup_hist_kernel(DupSrc src, const uint32_t* __restrict__ first_rec,
+__global__ void __launch_bounds__(RS_THREADS, 4) dup_hist_kernel(DupSrc src, const uint32_t* __restrict__ first_rec,
                                                              Count Kc, uint32_t* __restrict__ keys,
                                                              uint32_t* __restrict__ vals,
                                                              uint32_t* __restrict__ counts, uint32_t nblocks) {
@@ -664,6 +672,11 @@ void scan_u32_to_u64(const uint32_t* in, unsigned long long* out, uint64_t n, vo
     scan_impl(LoadDirect<uint32_t, unsigned long long>{in}, out, n, true, (unsigned long long*)nullptr, tmp, s);
 }
 
+void scan_u32_to_u64_count(const uint32_t* in, unsigned long long* out, Count n, unsigned long long* total,
+                           void* tmp, cudaStream_t s) {
+    scan_impl(LoadDirect<uint32_t, unsigned long long>{in}, out, n, true, total, tmp, s);
+}
+
 void scan_gather_u32_to_u64(const uint32_t* in, const uint32_t* idx, unsigned long long* out, Count n,
                             unsigned long long* total, void* tmp, cudaStream_t s) {
     scan_impl(LoadGather<unsigned long long>{in, idx}, out, n, true, total, tmp, s);
@@ -695,32 +708,32 @@ void radix_pass(uint64_t n, void* tmp, cudaStream_t s, Up up, Down down) {
 }
 }  // namespace
 
-void radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b, uint32_t* vals_out,
-                      Count n, int bits, void* tmp, cudaStream_t s) {
+void radix_sort_pairs(const uint32_t* keys0, const uint32_t* vals0, uint32_t* keys_a, uint32_t* vals_a,
+                      uint32_t* keys_b, uint32_t* vals_b, uint32_t* vals_out, Count n, int bits, void* tmp,
+                      cudaStream_t s, const uint32_t* gather_src, uint32_t* gather_out) {
     if (n.max == 0) return;
-    const int passes = (bits + 7) / 8;
-    if (passes == 0) {
-        cudaMemcpyAsync(vals_out, vals_a, n.max * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
-        return;
-    }
-    uint32_t *kin = keys_a, *vin = vals_a, *kout = keys_b, *vout = vals_b;
+    const int passes = (bits + 7) / 8 > 0 ? (bits + 7) / 8 : 1;
+    // pass 0 reads (keys0, vals0); later passes ping-pong b -> a -> b ...
+    const uint32_t* kin = keys0;
+    const uint32_t* vin = vals0;
     for (int p = 0; p < passes; p++) {
         const bool last = p == passes - 1;
-        if (last) vout = vals_out;
+        uint32_t* kout = (p & 1) ? keys_a : keys_b;
+        uint32_t* vout = last ? vals_out : ((p & 1) ? vals_a : vals_b);
         const int shift = 8 * p;
+        const uint32_t* gs = last ? gather_src : nullptr;
+        uint32_t* go = last ? gather_out : nullptr;
         radix_pass(
             n.max, tmp, s,
             [&](unsigned nb, uint32_t* counts) { rs_upsweep<<<nb, RS_THREADS, 0, s>>>(kin, n, shift, counts, nb); },
             [&](unsigned nb, uint32_t* counts) {
-                if (last) rs_downsweep<false><<<nb, RS_THREADS, 0, s>>>(kin, vin, kout, vout, n, shift, counts, nb);
-                else rs_downsweep<true><<<nb, RS_THREADS, 0, s>>>(kin, vin, kout, vout, n, shift, counts, nb);
+                if (last)
+                    rs_downsweep<false><<<nb, RS_THREADS, 0, s>>>(kin, vin, kout, vout, n, shift, counts, nb, gs, go);
+                else
+                    rs_downsweep<true><<<nb, RS_THREADS, 0, s>>>(kin, vin, kout, vout, n, shift, counts, nb);
             });
-        uint32_t* nk = kin;
-        uint32_t* nv = vin;
         kin = kout;
         vin = vout;
-        kout = nk;
-        vout = (nv == vals_a || nv == vals_b) ? nv : vals_a;
     }
 }
 
