@@ -451,8 +451,10 @@ def run_ours(args, rank, world):
 
     # ---- the secondary workload: batched step and per-view loop ----
     secondary = None
+    memory = None
     if not args.no_secondary and args.workload != SECONDARY_WORKLOAD:
         secondary = run_secondary(args, torch, mvgs, timed)
+        memory = run_memory(torch, mvgs)
 
     # ---- serving loop: resident 2M SH-3 scene, Poisson arrivals ----
     serving = None
@@ -500,6 +502,7 @@ def run_ours(args, rank, world):
         "training_kernels": training,
         "serving": serving,
         "secondary_workload": secondary,
+        "memory_at_differentiation_scale": memory,
         "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in (stages or {}).items() if v[1]},
         "roofline": roof,
         "stage_roofline": per_stage,
@@ -563,6 +566,46 @@ def run_secondary(args, torch, mvgs, timed):
            "per_view_loop": {"views_per_s": V / (ms_l / 1e3), "ms_per_step": ms_l,
                              "speedup_batched_over_loop": ms_l / ms_b}, "steps": steps}
     del batch, singles, params, grads, acc, acc_grads
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_memory(torch, mvgs):
+    """Device memory of one differentiable step at the differentiation scale
+    (1M SH-3 Gaussians, 16 views of 1024x768) against a 20 GB activation
+    budget: the blend state kept from the forward for the backward (sorted
+    lists, final transmittance and last contributor per pixel: the backward
+    recomputes each pixel's transmittances from them instead of storing
+    per-pixel lists), the workspace, and the torch allocator's peak over a
+    forward + backward through the autograd function (parameters and their
+    gradients included)."""
+    from paper_2506_12727_gb300 import autograd
+    dev = "cuda"
+    scene, cams, _ = synth.workload("diff_1m_16x1024x768")
+    params = {k: torch.tensor(getattr(scene, k), device=dev).contiguous() for k in
+              ("means", "log_scales", "quats", "opacity_logits", "sh")}
+    rz = mvgs.Rasterizer(cams, tile=(16, 64))
+    need = rz.reserve_for(mvgs.make_scene(params, scene.sh_degree))
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
+    base = torch.cuda.memory_allocated()
+    ps = {k: v.clone().requires_grad_(True) for k, v in params.items()}
+    img = autograd.render(rz, ps, scene.sh_degree)
+    img.sum().backward()
+    torch.cuda.synchronize()
+    peak = torch.cuda.max_memory_allocated() - base
+    L = rz.layout
+    # what storing each blended pair's state would cost instead (4 bytes of
+    # transmittance per pair), from the pixels' blend statistics
+    rz.forward(mvgs.make_scene(params, scene.sh_degree), stats=True)
+    blended = int(rz.records()["pixel_stats"].to(torch.int64)[:, 1].sum().item())
+    out = {"workload": "diff_1m_16x1024x768", "records": int(need.records), "keys": int(need.keys),
+           "state_bytes": int(L.state_bytes), "workspace_bytes": int(L.workspace_bytes),
+           "step_peak_bytes": int(peak), "budget_bytes": 20 * 10**9,
+           "stored_per_pair_state_bytes": 4 * blended,
+           "reading": "the backward recomputes the transmittances from the final T and the last contributor; "
+                      "state + workspace and the step's peak are the bytes against the 20 GB budget"}
+    del ps, img, rz, params
     torch.cuda.empty_cache()
     return out
 
