@@ -283,6 +283,43 @@ __global__ void __launch_bounds__(RS_THREADS) rs_upsweep(const uint32_t* __restr
 // vin == nullptr: the values are the keys' positions (an identity
 // permutation, generated instead of read).  gout != nullptr: also writes
 // gout[pos] = gsrc[value] (a per-element array carried into sorted order).
+// The same table for a pass whose digits take at most 32 values (the tile
+// sort's last pass over the tile ids' high bits): each lane counts into its
+// own column of a per-warp table (digit-major, lane-minor: a lane's updates
+// hit its own bank, and are plain read-modify-writes, not atomics, since no
+// other lane touches the column), then a skewed sweep sums the columns.
+// Shared-memory atomics from 32 lanes on a handful of digits serialise.
+__global__ void __launch_bounds__(RS_THREADS) rs_upsweep_narrow(const uint32_t* __restrict__ keys, Count cn, int shift,
+                                                               uint32_t mask, uint32_t* __restrict__ counts,
+                                                               uint32_t nblocks) {
+    __shared__ uint32_t cnt[RS_WARPS][32 * 32];
+    __shared__ uint32_t wsum[RS_WARPS][32];
+    const uint64_t n = cn.get();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* c = cnt[warp];
+    for (int i = lane; i < 32 * 32; i += 32) c[i] = 0;
+    __syncwarp();
+    const uint64_t base = (uint64_t)blockIdx.x * RS_TILE + warp * RS_SEG + lane;
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; j++) {
+        const uint64_t idx = base + (uint64_t)j * 32;
+        if (idx < n) c[((keys[idx] >> shift) & mask) * 32 + lane] += 1u;
+    }
+    __syncwarp();
+    // lane d sums digit d's column, starting at a different lane per digit
+    uint32_t sum = 0;
+#pragma unroll 8
+    for (int i = 0; i < 32; i++) sum += c[lane * 32 + ((i + lane) & 31)];
+    wsum[warp][lane] = sum;
+    __syncthreads();
+    uint32_t total = 0;
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; w++) total += wsum[w][threadIdx.x];
+    }
+    counts[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = threadIdx.x < 32 ? total : 0u;
+}
+
 template <bool WRITE_KEYS>
 __global__ void __launch_bounds__(RS_THREADS, 3) rs_downsweep(const uint32_t* __restrict__ kin,
                                                              const uint32_t* __restrict__ vin,
@@ -758,6 +795,9 @@ void tile_sort(const uint32_t* order, const unsigned long long* tile_off, Count 
                     block_starts_kernel<<<(unsigned)ceil_div_u64(R.max, 256), 256, 0, s>>>(tile_off, R, nb, first_rec);
                     dup_hist_kernel<<<nb, RS_THREADS, 0, s>>>(src, first_rec, K, keys_a, vals_a, counts, nb);
                     note_launches(1);
+                } else if (bits - shift <= 5) {
+                    rs_upsweep_narrow<<<nb, RS_THREADS, 0, s>>>(kin, K, shift, (1u << (bits - shift)) - 1u, counts,
+                                                                nb);
                 } else {
                     rs_upsweep<<<nb, RS_THREADS, 0, s>>>(kin, K, shift, counts, nb);
                 }
