@@ -187,7 +187,7 @@ struct RankSmem {
 // in runs of consecutive positions per digit.  Equal digits inside a round are
 // found with one ballot per digit bit.  Values are fetched after the ranking
 // (get_val(block-local index)), so they do not occupy registers during it.
-template <bool WRITE_KEYS, class GetVal>
+template <bool WRITE_KEYS, int NB, class GetVal>
 __device__ __forceinline__ void rank_and_scatter(RankSmem& sm, const uint32_t (&k)[RS_ITEMS], uint64_t n, int shift,
                                                  const uint32_t* __restrict__ offsets, uint32_t nblocks,
                                                  uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
@@ -209,7 +209,7 @@ __device__ __forceinline__ void rank_and_scatter(RankSmem& sm, const uint32_t (&
         const uint32_t d = (k[j] >> shift) & 0xffu;
         uint32_t peers = __ballot_sync(kFull, ok);
 #pragma unroll
-        for (int b = 0; b < 8; b++) {
+        for (int b = 0; b < NB; b++) {  // digit bits above NB are zero in this pass
             const uint32_t bit = (d >> b) & 1u;
             const uint32_t bb = __ballot_sync(kFull, bit);
             peers &= bit ? bb : ~bb;
@@ -320,7 +320,9 @@ __global__ void __launch_bounds__(RS_THREADS) rs_upsweep_narrow(const uint32_t* 
     counts[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = threadIdx.x < 32 ? total : 0u;
 }
 
-template <bool WRITE_KEYS>
+// NB: significant bits of this pass's digit (8, or fewer in a last pass over
+// the high bits of keys narrower than a whole number of digits).
+template <bool WRITE_KEYS, int NB = 8>
 __global__ void __launch_bounds__(RS_THREADS, 3) rs_downsweep(const uint32_t* __restrict__ kin,
                                                              const uint32_t* __restrict__ vin,
                                                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(RS_THREADS, 3) rs_downsweep(const uint32_t* __
         const uint64_t idx = base + (uint64_t)j * 32;
         k[j] = idx < n ? kin[idx] : 0u;
     }
-    rank_and_scatter<WRITE_KEYS>(
+    rank_and_scatter<WRITE_KEYS, NB>(
         sm, k, n, shift, offsets, nblocks, kout, vout,
         [&](int local) { return vin ? vin[block0 + local] : (uint32_t)(block0 + local); }, gsrc, gout);
 }
@@ -803,7 +805,9 @@ void tile_sort(const uint32_t* order, const unsigned long long* tile_off, Count 
                 }
             },
             [&](unsigned nb, uint32_t* counts) {
-                if (last) rs_downsweep<false><<<nb, RS_THREADS, 0, s>>>(kin, vin, kout, vout, K, shift, counts, nb);
+                if (last && bits - shift <= 5)
+                    rs_downsweep<false, 5><<<nb, RS_THREADS, 0, s>>>(kin, vin, kout, vout, K, shift, counts, nb);
+                else if (last) rs_downsweep<false><<<nb, RS_THREADS, 0, s>>>(kin, vin, kout, vout, K, shift, counts, nb);
                 else rs_downsweep<true><<<nb, RS_THREADS, 0, s>>>(kin, vin, kout, vout, K, shift, counts, nb);
             });
         uint32_t* nk = kin;
