@@ -406,11 +406,13 @@ mvgs_status mvgs_dssim_loss(const float* img, const float* target, const int32_t
  * results as mvgs_dssim_loss minus the workspace: the scratch is an 80 MiB
  * static device array inside the library (every GPU that loads the library
  * holds it until exit), enough for about 2.2 million pixels per call (one
- * 1920x1080 view); larger calls return MVGS_ENOSPACE without launching.  The
- * first call on a device looks up the array's address on that device (make
- * that call before any stream capture) and keeps it for the life of the
- * process (not valid after cudaDeviceReset).  Calls share the array, so calls
- * that overlap on the GPU race; nothing in it needs clearing between calls. */
+ * 1920x1080 view); larger calls return MVGS_ENOSPACE without launching.  Each
+ * call outside stream capture looks up the array's address on the current
+ * device and caches it; a call under capture uses the cached address, so make
+ * a device's first call before any capture (a first call under capture returns
+ * MVGS_ECUDA without launching).  Calls share the array, so calls that overlap
+ * on the GPU race; nothing in it needs clearing between calls.  Timed as the
+ * D-SSIM stage when stage timing is on. */
 mvgs_status mvgs_dssim_loss_noalloc(const float* img, const float* target, const int32_t* hw, int32_t V,
                                     float lambda, float* loss_per_view, float* dL_dimg, mvgs_stream stream);
 

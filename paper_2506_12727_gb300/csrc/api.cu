@@ -79,30 +79,26 @@ Profiler& profiler() {
     return p;
 }
 
-// Records events around one stage when timing is enabled.
-class StageTimer {
-  public:
-    StageTimer(int stage, cudaStream_t s) : stage_(stage), s_(s) {
-        Profiler& p = profiler();
-        std::lock_guard<std::mutex> lk(p.mu);
-        if (!p.on) return;
-        a_ = p.get();
-        b_ = p.get();
-        cudaEventRecord(a_, s_);
-    }
-    ~StageTimer() {
-        if (!a_) return;
-        Profiler& p = profiler();
-        std::lock_guard<std::mutex> lk(p.mu);
-        cudaEventRecord(b_, s_);
-        p.pending.push_back({stage_, a_, b_});
-    }
+}  // namespace
 
-  private:
-    int stage_;
-    cudaStream_t s_;
-    cudaEvent_t a_ = nullptr, b_ = nullptr;
-};
+mvgs::StageTimer::StageTimer(int stage, cudaStream_t s) : stage_(stage), s_(s) {
+    Profiler& p = profiler();
+    std::lock_guard<std::mutex> lk(p.mu);
+    if (!p.on) return;
+    a_ = p.get();
+    b_ = p.get();
+    cudaEventRecord(a_, s_);
+}
+
+mvgs::StageTimer::~StageTimer() {
+    if (!a_) return;
+    Profiler& p = profiler();
+    std::lock_guard<std::mutex> lk(p.mu);
+    cudaEventRecord(b_, s_);
+    p.pending.push_back({stage_, a_, b_});
+}
+
+namespace {
 
 const char* kStageNames[MVGS_STAGE_COUNT] = {"count_visible", "scan_records", "preprocess", "depth_sort",
                                              "scan_tiles", "tile_sort", "ranges", "blend_forward",

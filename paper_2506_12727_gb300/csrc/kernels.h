@@ -15,6 +15,21 @@ void note_launches(int k);
 // Sets the calling thread's last error message (api.cu) and returns `st`.
 int record_error(int st, const char* msg);
 
+// Records events around one stage on `s` while stage timing is enabled
+// (mvgs_profile_enable); the totals are read by mvgs_profile_read (api.cu).
+class StageTimer {
+  public:
+    StageTimer(int stage, cudaStream_t s);
+    ~StageTimer();
+    StageTimer(const StageTimer&) = delete;
+    StageTimer& operator=(const StageTimer&) = delete;
+
+  private:
+    int stage_;
+    cudaStream_t s_;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
 // ---- preprocess.cu -------------------------------------------------------
 void upload_cams(const DevCam* host, int V, DevCam* dst, cudaStream_t s);
 

@@ -11,11 +11,10 @@
 //
 // The array is static device storage: every GPU that loads the library holds
 // kScratchBytes of it until the process exits.  Its device address is looked
-// up once per device (the first call on that device, with that device
-// current) and cached for the life of the process; that first call should
-// therefore come before any stream capture, and, like every device pointer
-// taken before it, the cached address is not valid after cudaDeviceReset
-// (do not call this entry point after resetting the device).  All calls share the array and it keeps the previous call's
+// up on every call made outside stream capture and cached per device; a call
+// under capture uses the cached address, so a device's first call must come
+// before any capture (a first call under capture returns MVGS_ECUDA without
+// launching).  All calls share the array and it keeps the previous call's
 // contents; the loss kernels write every scratch value before reading it, so
 // nothing needs clearing, but calls that overlap on the GPU (different
 // streams, no ordering between them) race on the array.
@@ -37,14 +36,23 @@ std::mutex g_mu;
 std::unordered_map<int, void*> g_device_ptr;
 
 // Device address of the scratch array on the current device (nullptr and a
-// CUDA error when the lookup fails).
-void* scratch_ptr(cudaError_t& err) {
+// CUDA error when the lookup fails).  Looked up again on every call that is
+// not under stream capture (the address follows the device's current
+// context, e.g. after cudaDeviceReset); a call under capture takes the
+// address cached by the device's last call outside capture.
+void* scratch_ptr(cudaStream_t stream, cudaError_t& err) {
     int dev = 0;
     err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return nullptr;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    err = cudaStreamIsCapturing(stream, &cap);
+    if (err != cudaSuccess) return nullptr;
     std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_device_ptr.find(dev);
-    if (it != g_device_ptr.end()) return it->second;
+    if (cap != cudaStreamCaptureStatusNone) {
+        auto it = g_device_ptr.find(dev);
+        if (it == g_device_ptr.end()) err = cudaErrorStreamCaptureUnsupported;
+        return it == g_device_ptr.end() ? nullptr : it->second;
+    }
     void* p = nullptr;
     err = cudaGetSymbolAddress(&p, g_dssim_scratch);
     if (err != cudaSuccess || p == nullptr) return nullptr;
@@ -70,9 +78,13 @@ extern "C" mvgs_status mvgs_dssim_loss_noalloc(const float* img, const float* ta
                             "these views need more scratch than the library's static buffer holds "
                             "(80 MiB, about 2.2 million pixels per call); use mvgs_dssim_loss with a workspace");
     cudaError_t err = cudaSuccess;
-    void* scratch = scratch_ptr(err);
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    void* scratch = scratch_ptr(s, err);
     if (!scratch) return record_error(MVGS_ECUDA, cudaGetErrorString(err));
-    launch_dssim(img, target, hw, V, lambda, loss_per_view, dL_dimg, scratch, reinterpret_cast<cudaStream_t>(stream));
+    {
+        StageTimer t(MVGS_STAGE_DSSIM, s);
+        launch_dssim(img, target, hw, V, lambda, loss_per_view, dL_dimg, scratch, s);
+    }
     err = cudaGetLastError();
     if (err != cudaSuccess) return record_error(MVGS_ECUDA, cudaGetErrorString(err));
     return MVGS_OK;

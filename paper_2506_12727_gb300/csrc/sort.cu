@@ -181,18 +181,26 @@ struct RankSmem {
     uint32_t svals[RS_TILE + 1];     // values in block-local sorted order (+1: see dup_downsweep)
 };
 
+// How a pass stores its output.  A two-pass sort of keys of at most 16 bits
+// whose values fit beside the high key bits in one word packs the first pass's
+// output: word = (key >> 8) << vb | value (vb value bits); the second pass
+// sorts these words on bits [vb, 32) and writes word & (2^vb - 1).
+enum PassMode { kPlain = 0, kPackOut = 1, kPackIn = 2 };
+
 // Stable rank of the block's keys (held in registers, warp w owning the
 // contiguous segment [w*SEG, (w+1)*SEG) in rounds of 32 lanes) and scatter:
 // first into shared memory in block-local digit order, then to global memory
 // in runs of consecutive positions per digit.  Equal digits inside a round are
 // found with one ballot per digit bit.  Values are fetched after the ranking
 // (get_val(block-local index)), so they do not occupy registers during it.
-template <bool WRITE_KEYS, int NB, class GetVal>
+// MODE kPackOut writes packed words to kout (shift 0); kPackIn takes the
+// values from the packed words and writes them to vout (shift vb).
+template <bool WRITE_KEYS, int NB, int MODE, class GetVal>
 __device__ __forceinline__ void rank_and_scatter(RankSmem& sm, const uint32_t (&k)[RS_ITEMS], uint64_t n, int shift,
                                                  const uint32_t* __restrict__ offsets, uint32_t nblocks,
                                                  uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                                 GetVal get_val, const uint32_t* __restrict__ gsrc = nullptr,
-                                                 uint32_t* __restrict__ gout = nullptr) {
+                                                 GetVal get_val, const uint32_t* __restrict__ gsrc,
+                                                 uint32_t* __restrict__ gout, int vb) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const uint64_t block0 = (uint64_t)blockIdx.x * RS_TILE;
@@ -224,8 +232,10 @@ __device__ __forceinline__ void rank_and_scatter(RankSmem& sm, const uint32_t (&
     // values are read before the barrier that precedes the scatter, so a
     // source may keep them in the staging the scatter overwrites
     uint32_t vv[RS_ITEMS];
+    if (MODE != kPackIn) {
 #pragma unroll
-    for (int j = 0; j < RS_ITEMS; j++) vv[j] = base + (uint64_t)j * 32 < n ? get_val(local0 + j * 32) : 0u;
+        for (int j = 0; j < RS_ITEMS; j++) vv[j] = base + (uint64_t)j * 32 < n ? get_val(local0 + j * 32) : 0u;
+    }
     __syncthreads();
     uint32_t run = 0;
 #pragma unroll
@@ -243,7 +253,7 @@ __device__ __forceinline__ void rank_and_scatter(RankSmem& sm, const uint32_t (&
             const uint32_t d = (k[j] >> shift) & 0xffu;
             const uint32_t lp = sm.dstart[d] + wh[d] + lr[j];
             sm.skeys[lp] = k[j];
-            sm.svals[lp] = vv[j];
+            if (MODE != kPackIn) sm.svals[lp] = vv[j];
         }
     }
     __syncthreads();
@@ -252,9 +262,15 @@ __device__ __forceinline__ void rank_and_scatter(RankSmem& sm, const uint32_t (&
         const uint32_t key = sm.skeys[i];
         const uint32_t d = (key >> shift) & 0xffu;
         const uint32_t pos = sm.boff[d] + (uint32_t)i - sm.dstart[d];
-        vout[pos] = sm.svals[i];
-        if (WRITE_KEYS) kout[pos] = key;
-        if (gout) gout[pos] = gsrc[sm.svals[i]];
+        if (MODE == kPackOut) {
+            kout[pos] = (key >> 8) << vb | sm.svals[i];
+        } else if (MODE == kPackIn) {
+            vout[pos] = key & ((1u << vb) - 1u);
+        } else {
+            vout[pos] = sm.svals[i];
+            if (WRITE_KEYS) kout[pos] = key;
+            if (gout) gout[pos] = gsrc[sm.svals[i]];
+        }
     }
 }
 
@@ -321,15 +337,16 @@ __global__ void __launch_bounds__(RS_THREADS) rs_upsweep_narrow(const uint32_t* 
 }
 
 // NB: significant bits of this pass's digit (8, or fewer in a last pass over
-// the high bits of keys narrower than a whole number of digits).
-template <bool WRITE_KEYS, int NB = 8>
+// the high bits of keys narrower than a whole number of digits); MODE and vb:
+// see PassMode.
+template <bool WRITE_KEYS, int NB = 8, int MODE = kPlain>
 __global__ void __launch_bounds__(RS_THREADS, 3) rs_downsweep(const uint32_t* __restrict__ kin,
                                                              const uint32_t* __restrict__ vin,
                                                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                              Count cn, int shift,
                                                              const uint32_t* __restrict__ offsets, uint32_t nblocks,
                                                              const uint32_t* __restrict__ gsrc = nullptr,
-                                                             uint32_t* __restrict__ gout = nullptr) {
+                                                             uint32_t* __restrict__ gout = nullptr, int vb = 0) {
     __shared__ RankSmem sm;
     const uint64_t n = cn.get();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -342,9 +359,9 @@ __global__ void __launch_bounds__(RS_THREADS, 3) rs_downsweep(const uint32_t* __
         const uint64_t idx = base + (uint64_t)j * 32;
         k[j] = idx < n ? kin[idx] : 0u;
     }
-    rank_and_scatter<WRITE_KEYS, NB>(
+    rank_and_scatter<WRITE_KEYS, NB, MODE>(
         sm, k, n, shift, offsets, nblocks, kout, vout,
-        [&](int local) { return vin ? vin[block0 + local] : (uint32_t)(block0 + local); }, gsrc, gout);
+        [&](int local) { return vin ? vin[block0 + local] : (uint32_t)(block0 + local); }, gsrc, gout, vb);
 }
 
 // ---------------------------------------------------------------------------
@@ -784,11 +801,17 @@ void tile_sort(const uint32_t* order, const unsigned long long* tile_off, Count 
     uint32_t* first_rec = reinterpret_cast<uint32_t*>(static_cast<char*>(tmp) + radix_temp_bytes(K.max));
     const DupSrc src{order, tile_off, R, rect, rec_v, cams, (uint32_t)tiles};
     const int passes = bits > 8 ? (bits + 7) / 8 : 1;
+    // record ids take vb bits; two passes whose second digit fits beside them
+    // in one word run packed (PassMode)
+    int vb = 1;
+    while (vb < 32 && (R.max - 1) >> vb) vb++;
+    const bool packed = passes == 2 && (bits - 8) + vb <= 32;
     uint32_t *kin = keys_a, *vin = vals_a, *kout = keys_b, *vout = vals_b;
     for (int p = 0; p < passes; p++) {
         const bool last = p == passes - 1;
         if (last) vout = vals_out;
-        const int shift = 8 * p;
+        const int shift = packed && last ? vb : 8 * p;
+        const int hi = bits - 8 * p;  // significant bits of this pass's digit
         radix_pass(
             K.max, tmp, s,
             [&](unsigned nb, uint32_t* counts) {
@@ -797,15 +820,23 @@ void tile_sort(const uint32_t* order, const unsigned long long* tile_off, Count 
                     block_starts_kernel<<<(unsigned)ceil_div_u64(R.max, 256), 256, 0, s>>>(tile_off, R, nb, first_rec);
                     dup_hist_kernel<<<nb, RS_THREADS, 0, s>>>(src, first_rec, K, keys_a, vals_a, counts, nb);
                     note_launches(1);
-                } else if (bits - shift <= 5) {
-                    rs_upsweep_narrow<<<nb, RS_THREADS, 0, s>>>(kin, K, shift, (1u << (bits - shift)) - 1u, counts,
-                                                                nb);
+                } else if (hi <= 5) {
+                    rs_upsweep_narrow<<<nb, RS_THREADS, 0, s>>>(kin, K, shift, (1u << hi) - 1u, counts, nb);
                 } else {
                     rs_upsweep<<<nb, RS_THREADS, 0, s>>>(kin, K, shift, counts, nb);
                 }
             },
             [&](unsigned nb, uint32_t* counts) {
-                if (last && bits - shift <= 5)
+                if (packed && !last)
+                    rs_downsweep<true, 8, kPackOut><<<nb, RS_THREADS, 0, s>>>(kin, vin, kout, nullptr, K, shift, counts,
+                                                                               nb, nullptr, nullptr, vb);
+                else if (packed && hi <= 5)
+                    rs_downsweep<false, 5, kPackIn><<<nb, RS_THREADS, 0, s>>>(kin, nullptr, nullptr, vout, K, shift,
+                                                                               counts, nb, nullptr, nullptr, vb);
+                else if (packed)
+                    rs_downsweep<false, 8, kPackIn><<<nb, RS_THREADS, 0, s>>>(kin, nullptr, nullptr, vout, K, shift,
+                                                                               counts, nb, nullptr, nullptr, vb);
+                else if (last && hi <= 5)
                     rs_downsweep<false, 5><<<nb, RS_THREADS, 0, s>>>(kin, vin, kout, vout, K, shift, counts, nb);
                 else if (last) rs_downsweep<false><<<nb, RS_THREADS, 0, s>>>(kin, vin, kout, vout, K, shift, counts, nb);
                 else rs_downsweep<true><<<nb, RS_THREADS, 0, s>>>(kin, vin, kout, vout, K, shift, counts, nb);

@@ -7,7 +7,8 @@ loss's scratch in a static device array instead of a caller workspace.  Its
 results must equal mvgs_dssim_loss's bit for bit on the same inputs (both run
 the same deterministic kernels), with and without the gradient output, on
 consecutive calls (the array keeps the previous call's contents), and calls
-too large for the array must be refused without running.
+too large for the array must be refused without running.  With stage timing
+on, its launches count as the D-SSIM stage.
 """
 import numpy as np
 import pytest
@@ -60,3 +61,19 @@ def test_noalloc_refuses_calls_larger_than_its_buffer(cuda_lib):
         mvgs.dssim_loss_noalloc(img, img, hw, 0.2, loss, None)
     assert e.value.status == mvgs.ENOSPACE
     assert "static buffer" in mvgs.last_error()
+
+
+def test_noalloc_is_timed_as_the_dssim_stage(cuda_lib):
+    mvgs = cuda_lib
+    img, tgt, hw = _case(np.random.default_rng(62), [(64, 96)])
+    loss = torch.empty(1, device="cuda")
+    mvgs.profile_read()
+    mvgs.profile_enable(True)
+    try:
+        for _ in range(3):
+            mvgs.dssim_loss_noalloc(img, tgt, hw, 0.2, loss, None)
+        torch.cuda.synchronize()
+    finally:
+        mvgs.profile_enable(False)
+    ms, calls = mvgs.profile_read()["dssim"]
+    assert calls == 3 and ms > 0
