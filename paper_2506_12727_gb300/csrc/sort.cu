@@ -184,7 +184,8 @@ struct RankSmem {
 // How a pass stores its output.  A two-pass sort of keys of at most 16 bits
 // whose values fit beside the high key bits in one word packs the first pass's
 // output: word = (key >> 8) << vb | value (vb value bits); the second pass
-// sorts these words on bits [vb, 32) and writes word & (2^vb - 1).
+// sorts these words on bits [vb, 32) and writes word & (2^vb - 1).  The first
+// pass of such a sort reads its keys as 16-bit words.
 enum PassMode { kPlain = 0, kPackOut = 1, kPackIn = 2 };
 
 // Stable rank of the block's keys (held in registers, warp w owning the
@@ -357,7 +358,8 @@ __global__ void __launch_bounds__(RS_THREADS, 3) rs_downsweep(const uint32_t* __
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; j++) {
         const uint64_t idx = base + (uint64_t)j * 32;
-        k[j] = idx < n ? kin[idx] : 0u;
+        // kPackOut reads the 16-bit keys of a two-pass sort
+        k[j] = idx >= n ? 0u : MODE == kPackOut ? (uint32_t)reinterpret_cast<const uint16_t*>(kin)[idx] : kin[idx];
     }
     rank_and_scatter<WRITE_KEYS, NB, MODE>(
         sm, k, n, shift, offsets, nblocks, kout, vout,
@@ -423,18 +425,27 @@ __global__ void block_starts_kernel(const unsigned long long* __restrict__ off, 
     for (uint64_t b = b0; b < b1 && b < nblocks; b++) first[b] = (uint32_t)r;
 }
 
+// K16: keys stored as 16-bit words (tile ids below 2^16; see PassMode).
+template <bool K16>
 __global__ void __launch_bounds__(RS_THREADS, 4) dup_hist_kernel(DupSrc src, const uint32_t* __restrict__ first_rec,
                                                              Count Kc, uint32_t* __restrict__ keys,
                                                              uint32_t* __restrict__ vals,
                                                              uint32_t* __restrict__ counts, uint32_t nblocks) {
     __shared__ uint32_t hist[RS_WARPS * 256];
-    __shared__ int s_off[RS_TILE + 2];
-    // the block's records, gathered once by all threads together (their
-    // loads are independent, so they are all in flight at once) instead of
-    // one dependent chain order -> rect, view -> camera per thread and record
-    __shared__ uint32_t s_rec[DUP_MAXR], s_base[DUP_MAXR];
-    __shared__ short4 s_rect[DUP_MAXR];
-    __shared__ int s_tx[DUP_MAXR];
+    // the block's record offsets and records (gathered once by all threads
+    // together: their loads are independent, so they are all in flight at
+    // once, instead of one dependent chain order -> rect, view -> camera per
+    // thread and record); after the generation the same bytes stage the
+    // block's entries for coalesced stores
+    constexpr int OFF_BYTES = (RS_TILE + 4) * 4;
+    constexpr int RAW_BYTES = OFF_BYTES + DUP_MAXR * 20;
+    static_assert(RAW_BYTES >= RS_TILE * 8, "entry staging");
+    __shared__ __align__(16) unsigned char s_raw[RAW_BYTES];
+    int* s_off = reinterpret_cast<int*>(s_raw);
+    short4* s_rect = reinterpret_cast<short4*>(s_raw + OFF_BYTES);
+    uint32_t* s_rec = reinterpret_cast<uint32_t*>(s_raw + OFF_BYTES + DUP_MAXR * 8);
+    uint32_t* s_base = s_rec + DUP_MAXR;
+    int* s_tx = reinterpret_cast<int*>(s_base + DUP_MAXR);
     const uint64_t K = Kc.get();
     const uint64_t k0 = (uint64_t)blockIdx.x * RS_TILE;
     if (k0 >= K) {  // a block past the entries (capturable mode): empty histogram
@@ -519,24 +530,60 @@ __global__ void __launch_bounds__(RS_THREADS, 4) dup_hist_kernel(DupSrc src, con
                 }
             }
         }
-        if (first + DUP_ITEMS <= K) {
-            uint4* kq = reinterpret_cast<uint4*>(keys + first);
-            uint4* vq = reinterpret_cast<uint4*>(vals + first);
+    }
+    // stage the entries, then store them coalesced.  Thread t's quads of
+    // 32-bit words go to slots 4t + ((q + t/2) & 3), its pairs of 8 16-bit
+    // keys to 2t + ((q + t/4) & 1): the eight threads of a 128-byte phase hit
+    // distinct banks.
+    __syncthreads();
+    uint4* sv = reinterpret_cast<uint4*>(s_raw);
+    uint4* sk = sv + RS_TILE / 4;
+    const int t = threadIdx.x;
 #pragma unroll
-            for (int q = 0; q < DUP_ITEMS / 4; q++) {
-                kq[q] = make_uint4(kk[4 * q], kk[4 * q + 1], kk[4 * q + 2], kk[4 * q + 3]);
-                vq[q] = make_uint4(vv[4 * q], vv[4 * q + 1], vv[4 * q + 2], vv[4 * q + 3]);
-            }
-        } else {
+    for (int q = 0; q < DUP_ITEMS / 4; q++)
+        sv[4 * t + ((q + (t >> 1)) & 3)] = make_uint4(vv[4 * q], vv[4 * q + 1], vv[4 * q + 2], vv[4 * q + 3]);
+    if (K16) {
 #pragma unroll
-            for (int i = 0; i < DUP_ITEMS; i++)
-                if (first + i < K) {
-                    keys[first + i] = kk[i];
-                    vals[first + i] = vv[i];
-                }
+        for (int q = 0; q < DUP_ITEMS / 8; q++) {
+            const uint32_t* h = kk + 8 * q;
+            sk[2 * t + ((q + (t >> 2)) & 1)] = make_uint4(h[0] | h[1] << 16, h[2] | h[3] << 16, h[4] | h[5] << 16,
+                                                          h[6] | h[7] << 16);
         }
+    } else {
+#pragma unroll
+        for (int q = 0; q < DUP_ITEMS / 4; q++)
+            sk[4 * t + ((q + (t >> 1)) & 3)] = make_uint4(kk[4 * q], kk[4 * q + 1], kk[4 * q + 2], kk[4 * q + 3]);
     }
     __syncthreads();
+    const uint64_t cnt = K - k0 < (uint64_t)RS_TILE ? K - k0 : (uint64_t)RS_TILE;
+    for (int L = t; L < RS_TILE / 4; L += RS_THREADS) {  // values, 4 per quad
+        const int owner = L >> 2;
+        const uint4 a = sv[4 * owner + (((L & 3) + (owner >> 1)) & 3)];
+        const uint64_t e = (uint64_t)L * 4;
+        if (e + 4 <= cnt) {
+            reinterpret_cast<uint4*>(vals + k0)[L] = a;
+        } else {
+            const uint32_t va[4] = {a.x, a.y, a.z, a.w};
+            for (int i = 0; i < 4 && e + i < cnt; i++) vals[k0 + e + i] = va[i];
+        }
+    }
+    constexpr int KPER = K16 ? 8 : 4;  // keys per quad
+    for (int L = t; L < RS_TILE / KPER; L += RS_THREADS) {
+        const int owner = K16 ? L >> 1 : L >> 2;
+        const uint4 a = K16 ? sk[2 * owner + (((L & 1) + (owner >> 2)) & 1)]
+                            : sk[4 * owner + (((L & 3) + (owner >> 1)) & 3)];
+        const uint64_t e = (uint64_t)L * KPER;
+        if (e + KPER <= cnt) {
+            if (K16) reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(keys) + k0)[L] = a;
+            else reinterpret_cast<uint4*>(keys + k0)[L] = a;
+        } else {
+            const uint32_t ka[4] = {a.x, a.y, a.z, a.w};
+            for (int i = 0; i < KPER && e + i < cnt; i++) {
+                if (K16) reinterpret_cast<uint16_t*>(keys)[k0 + e + i] = (uint16_t)(ka[i >> 1] >> (16 * (i & 1)));
+                else keys[k0 + e + i] = ka[i];
+            }
+        }
+    }
     uint32_t sum = 0;
 #pragma unroll
     for (int w2 = 0; w2 < RS_WARPS; w2++) sum += hist[w2 * 256 + threadIdx.x];
@@ -818,7 +865,10 @@ void tile_sort(const uint32_t* order, const unsigned long long* tile_off, Count 
                 // pass 0 writes the entries and the histogram of their first digit
                 if (p == 0) {
                     block_starts_kernel<<<(unsigned)ceil_div_u64(R.max, 256), 256, 0, s>>>(tile_off, R, nb, first_rec);
-                    dup_hist_kernel<<<nb, RS_THREADS, 0, s>>>(src, first_rec, K, keys_a, vals_a, counts, nb);
+                    if (packed)
+                        dup_hist_kernel<true><<<nb, RS_THREADS, 0, s>>>(src, first_rec, K, keys_a, vals_a, counts, nb);
+                    else
+                        dup_hist_kernel<false><<<nb, RS_THREADS, 0, s>>>(src, first_rec, K, keys_a, vals_a, counts, nb);
                     note_launches(1);
                 } else if (hi <= 5) {
                     rs_upsweep_narrow<<<nb, RS_THREADS, 0, s>>>(kin, K, shift, (1u << hi) - 1u, counts, nb);
