@@ -319,23 +319,40 @@ __global__ void __launch_bounds__(256) count_keys_kernel(SceneArgs sc, const Dev
 
 constexpr int PRE_THREADS = 128;
 
+// One lane per (Gaussian, view) pair: a warp takes 32 / VG consecutive
+// Gaussians with VG = min(V, 32) lanes each (views in order; more than 32
+// views go in chunks of 32), so a warp's visible pairs are consecutive records
+// of the Gaussian-major list and every record field is stored coalesced (one
+// thread per Gaussian stored its records about V records apart from the next
+// thread's: partly written sectors).  The lanes of a Gaussian read the same
+// parameters (broadcast loads).
 template <int DEG>
-__global__ void __launch_bounds__(PRE_THREADS) preprocess_kernel(SceneArgs sc, const DevCam* __restrict__ cams, int V, int tw,
-                                                         int th, const uint8_t* __restrict__ vis, RecordArgs rec,
-                                                         uint32_t* __restrict__ tiles_touched) {
+__global__ void __launch_bounds__(PRE_THREADS) preprocess_kernel(SceneArgs sc, const DevCam* __restrict__ cams, int V,
+                                                                 int tw, int th, const uint8_t* __restrict__ vis,
+                                                                 RecordArgs rec, uint32_t* __restrict__ tiles_touched) {
     constexpr int NK = (DEG + 1) * (DEG + 1);
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= sc.n) return;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int VG = V < 32 ? V : 32;
+    const int GPW = 32 / VG;
+    const long long g0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * GPW;
+    if (g0 >= sc.n) return;  // the whole warp
+    const int gi = lane / VG, vl = lane - gi * VG;
+    const long long g = g0 + gi;
+    const bool mine = gi < GPW && g < sc.n;
     Gauss G;
-    load_gauss(sc, g, G, true);
-    long long r = rec.rec_off[g];
-    const float* shg = sc.sh + (size_t)g * NK * 3;
+    if (mine) load_gauss(sc, g, G, true);
+    const float* shg = sc.sh + (size_t)(mine ? g : g0) * NK * 3;
     const bool sh_vec = (reinterpret_cast<uintptr_t>(sc.sh) & 15) == 0;  // rows of 48 floats stay 16-byte aligned
-    __shared__ float s_sh[NK * 3 * PRE_THREADS];
-    const float* shc = stage_sh<NK, PRE_THREADS>(shg, sh_vec, s_sh);
-    for (int v = 0; v < V; v++) {
-        if (!vis[g * V + v]) continue;
-        if (r >= rec.cap) break;  // capturable mode past its record capacity (reported through the counts)
+    long long rbase = rec.rec_off[g0];
+    for (int c = 0; c < V; c += VG) {
+        const int v = c + vl;
+        const bool on = mine && v < V && vis[g * V + v];
+        const uint32_t bal = __ballot_sync(0xffffffffu, on);
+        const long long r = rbase + __popc(bal & lt);
+        rbase += __popc(bal);
+        // capturable mode past its record capacity: not written (reported through the counts)
+        if (!on || r >= rec.cap) continue;
         const DevCam& cam = cams[v];
         Proj P;
         const bool ok = project(G, cam, tw, th, P);
@@ -353,8 +370,7 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_kernel(SceneArgs sc, c
         sh_basis<DEG>(dx, dy, dz, Y);
         float rgb[3] = {0.5f, 0.5f, 0.5f};
         int clamp = 0;
-#pragma unroll
-        for (int e = 0; e < NK * 3; e++) rgb[e % 3] += Y[e / 3] * shc[e * PRE_THREADS];
+        for_each_sh<NK>(shg, sh_vec, [&](int e, float coef) { rgb[e % 3] += Y[e / 3] * coef; });
 #pragma unroll
         for (int ch = 0; ch < 3; ch++) {
             if (rgb[ch] < 0.f) { clamp |= 1 << ch; rgb[ch] = 0.f; }
@@ -364,7 +380,6 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_kernel(SceneArgs sc, c
         rec.depth[r] = P.depth;
         rec.rect[r] = P.rect;
         tiles_touched[r] = (uint32_t)((P.rect.z - P.rect.x) * (P.rect.w - P.rect.y));
-        r++;
     }
 }
 
@@ -603,7 +618,9 @@ void launch_preprocess(const SceneArgs& sc, const DevCam* cams, int V, int tw, i
                        const RecordArgs& rec, uint32_t* tiles_touched,
                        cudaStream_t s) {
     if (sc.n == 0) return;
-    const unsigned nb = blocks_for(sc.n, PRE_THREADS);
+    const long long gpw = V < 32 ? 32 / V : 1;  // Gaussians per warp
+    const long long warps = (sc.n + gpw - 1) / gpw;
+    const unsigned nb = (unsigned)((warps + PRE_THREADS / 32 - 1) / (PRE_THREADS / 32));
 #define MVGS_PP(D) \
     preprocess_kernel<D><<<nb, PRE_THREADS, 0, s>>>(sc, cams, V, tw, th, vis, rec, tiles_touched)
     switch (sc.sh_degree) {
