@@ -57,7 +57,8 @@ typedef enum mvgs_status {
     MVGS_ENOSPACE = 2,    /* state or workspace too small, or a capacity exceeded;
                              the needed counts are reported and nothing is rendered */
     MVGS_EOVERFLOW = 3,   /* a count does not fit the index types (keys >= 2^32,
-                             records >= 2^31, global tiles >= 2^32) */
+                             records >= 2^31, global tiles >= 2^32, more than
+                             4095 tiles along one axis of a view) */
     MVGS_ECUDA = 4,       /* a CUDA launch or copy failed */
     MVGS_EDEVICE = 5      /* a device-side check failed (e.g. a bounded wait expired) */
 } mvgs_status;

@@ -122,7 +122,7 @@ struct Plan {
     mvgs_layout L{};
     // workspace offsets (forward)
     size_t w_cams = 0, w_counts = 0, w_vis = 0, w_scan = 0, w_dkeys_a = 0, w_dkeys_b = 0, w_ids_a = 0, w_ids_b = 0,
-           w_order = 0, w_tiles = 0, w_tile_off = 0, w_keys_a = 0, w_keys_b = 0, w_vals_a = 0, w_vals_b = 0,
+           w_order = 0, w_tiles = 0, w_desc = 0, w_tile_off = 0, w_keys_a = 0, w_keys_b = 0, w_vals_a = 0, w_vals_b = 0,
            w_radix = 0, w_tcount = 0, w_torder = 0, w_counter = 0, w_dcount = 0;
     // workspace offsets of the sampled blend (forward and backward each carve their own)
     size_t w_chunk_off = 0, w_chunk_map = 0, w_chunk_tmp = 0, w_mask = 0;
@@ -171,7 +171,8 @@ mvgs_status make_plan(long long n, const mvgs_camera* cams, int V, const mvgs_co
         if (c.width < 1 || c.height < 1) return fail(MVGS_EINVAL, "view %d: empty image", v);
         if (!(c.fx > 0.f) || !(c.fy > 0.f)) return fail(MVGS_EINVAL, "view %d: focal lengths must be > 0", v);
         const int txs = (c.width + tw - 1) / tw, tys = (c.height + th - 1) / th;
-        if (txs > 32767 || tys > 32767) return fail(MVGS_EOVERFLOW, "view %d: more than 32767 tiles per axis", v);
+        // tile coordinates travel in 12-bit fields of the duplication's record descriptors
+        if (txs > 4095 || tys > 4095) return fail(MVGS_EOVERFLOW, "view %d: more than 4095 tiles per axis", v);
         DevCam& d = P.cams[v];
         for (int i = 0; i < 3; i++) {
             for (int j = 0; j < 3; j++) d.R[3 * i + j] = c.viewmat[4 * i + j];
@@ -232,6 +233,7 @@ mvgs_status make_plan(long long n, const mvgs_camera* cams, int V, const mvgs_co
     P.w_ids_b = w.take(R * sizeof(uint32_t));
     P.w_order = w.take(R * sizeof(uint32_t));
     P.w_tiles = w.take(R * sizeof(uint32_t));
+    P.w_desc = w.take(R * sizeof(unsigned long long));
     P.w_tile_off = w.take((R + 1) * sizeof(unsigned long long));
     P.w_keys_a = w.take(K * sizeof(uint32_t));
     P.w_keys_b = w.take(K * sizeof(uint32_t));
@@ -501,11 +503,13 @@ static mvgs_status render_impl(const mvgs_scene* scene, const mvgs_camera* cams,
     }
     const Count Rc = capt ? Count((unsigned long long)cap->records, dcnt) : Count((unsigned long long)R);
 
-    // projection, colour, radius and tile rectangle of every record
+    // projection, colour, radius and tile rectangle of every record, its tile
+    // count and its tile descriptor (rectangle and view in 8 bytes)
     uint32_t* tiles = at<uint32_t>(workspace, P.w_tiles);
+    unsigned long long* desc = at<unsigned long long>(workspace, P.w_desc);
     {
         StageTimer t(MVGS_STAGE_PREPROCESS, s);
-        launch_preprocess(sc, dcams, V, tw, th, at<uint8_t>(workspace, P.w_vis), rec, tiles, s);
+        launch_preprocess(sc, dcams, V, tw, th, at<uint8_t>(workspace, P.w_vis), rec, tiles, desc, s);
     }
 
     // records by depth (the keys are the records' float32 depths, positive, so
@@ -545,7 +549,7 @@ static mvgs_status render_impl(const mvgs_scene* scene, const mvgs_camera* cams,
     uint32_t* sorted = at<uint32_t>(state, L.off_sorted_records);
     {
         StageTimer t(MVGS_STAGE_TILE_SORT, s);
-        tile_sort(order, tile_off, Rc, Kc, rec.rect, rec.rec_v, dcams, P.tiles, bits_for(P.tiles),
+        tile_sort(order, tile_off, Rc, Kc, desc, dcams, P.tiles, bits_for(P.tiles),
                   at<uint32_t>(workspace, P.w_keys_a), at<uint32_t>(workspace, P.w_vals_a),
                   at<uint32_t>(workspace, P.w_keys_b), at<uint32_t>(workspace, P.w_vals_b), sorted,
                   at<void>(workspace, P.w_radix), s);

@@ -132,6 +132,20 @@ __device__ __forceinline__ float3 conic_of(float4 q) {
     return make_float3(-2.f * LN2 * q.x, -LN2 * q.y, -2.f * LN2 * q.z);
 }
 
+// A record's tile rectangle and view for the duplication, in 8 bytes: the
+// corners x0, y0, x1, y1 (tile coordinates, end exclusive, each below 2^12)
+// in bits 0-47 and the view in bits 48-63.
+__device__ __forceinline__ unsigned long long pack_tile_desc(short4 rc, int view) {
+    return (unsigned long long)(uint16_t)rc.x | (unsigned long long)(uint16_t)rc.y << 12 |
+           (unsigned long long)(uint16_t)rc.z << 24 | (unsigned long long)(uint16_t)rc.w << 36 |
+           (unsigned long long)view << 48;
+}
+__device__ __forceinline__ short4 tile_desc_rect(unsigned long long d) {
+    return make_short4((short)(d & 0xfffu), (short)(d >> 12 & 0xfffu), (short)(d >> 24 & 0xfffu),
+                       (short)(d >> 36 & 0xfffu));
+}
+__device__ __forceinline__ int tile_desc_view(unsigned long long d) { return (int)(d >> 48); }
+
 struct ColTerms {
     float xx, x;  // qa dx^2 and qb dx
 };

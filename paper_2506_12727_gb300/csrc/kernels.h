@@ -63,11 +63,10 @@ void launch_count_keys(const SceneArgs& sc, const DevCam* cams, int V, int tw, i
 // vis: [n * V] bytes, 1 where (g, v) is visible; counts: visible views per Gaussian.
 void launch_count_visible(const SceneArgs& sc, const DevCam* cams, int V, int tw, int th, int* counts, uint8_t* vis,
                           cudaStream_t s);
-// Writes all records of the visible pairs; also the depth-sort keys (float
-// bits of the depth), the identity permutation, and the number of tiles each
-// record touches.
+// Writes all records of the visible pairs, the number of tiles each record
+// touches and its tile descriptor (pack_tile_desc).
 void launch_preprocess(const SceneArgs& sc, const DevCam* cams, int V, int tw, int th, const uint8_t* vis,
-                       const RecordArgs& rec, uint32_t* tiles_touched,
+                       const RecordArgs& rec, uint32_t* tiles_touched, unsigned long long* tile_desc,
                        cudaStream_t s);
 void launch_zero_f32(float* p, size_t count, cudaStream_t s);
 // rec_grad: [records, kGradStride] float (mean2d, -, -, -, opacity, rgb, e1 at
@@ -107,12 +106,13 @@ void radix_sort_pairs(const uint32_t* keys0, const uint32_t* vals0, uint32_t* ke
 
 // Stable sort, by global (view, tile) id, of one entry per (record, covered
 // tile) taken in the order of `order` (records sorted by depth); tile_off is
-// the exclusive scan of the records' tile counts in that order.  The entries
+// the exclusive scan of the records' tile counts in that order; desc holds the
+// records' tile descriptors (pack_tile_desc, record order).  The entries
 // are generated inside the first radix pass.  Sorted record ids end in
 // vals_out; keys_a/b and vals_a/b are scratch of K entries.
-void tile_sort(const uint32_t* order, const unsigned long long* tile_off, Count R, Count K, const short4* rect,
-               const int* rec_v, const DevCam* cams, long long tiles, int bits, uint32_t* keys_a, uint32_t* vals_a,
-               uint32_t* keys_b, uint32_t* vals_b, uint32_t* vals_out, void* tmp, cudaStream_t s);
+void tile_sort(const uint32_t* order, const unsigned long long* tile_off, Count R, Count K,
+               const unsigned long long* desc, const DevCam* cams, long long tiles, int bits, uint32_t* keys_a,
+               uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b, uint32_t* vals_out, void* tmp, cudaStream_t s);
 
 // Tiles ordered by decreasing list length (the blend's processing order).
 size_t tile_order_temp_bytes(long long tiles);

@@ -329,7 +329,8 @@ constexpr int PRE_THREADS = 128;
 template <int DEG>
 __global__ void __launch_bounds__(PRE_THREADS) preprocess_kernel(SceneArgs sc, const DevCam* __restrict__ cams, int V,
                                                                  int tw, int th, const uint8_t* __restrict__ vis,
-                                                                 RecordArgs rec, uint32_t* __restrict__ tiles_touched) {
+                                                                 RecordArgs rec, uint32_t* __restrict__ tiles_touched,
+                                                                 unsigned long long* __restrict__ tile_desc) {
     constexpr int NK = (DEG + 1) * (DEG + 1);
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
@@ -380,6 +381,7 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_kernel(SceneArgs sc, c
         rec.depth[r] = P.depth;
         rec.rect[r] = P.rect;
         tiles_touched[r] = (uint32_t)((P.rect.z - P.rect.x) * (P.rect.w - P.rect.y));
+        tile_desc[r] = pack_tile_desc(P.rect, v);
     }
 }
 
@@ -615,14 +617,14 @@ void launch_count_visible(const SceneArgs& sc, const DevCam* cams, int V, int tw
 }
 
 void launch_preprocess(const SceneArgs& sc, const DevCam* cams, int V, int tw, int th, const uint8_t* vis,
-                       const RecordArgs& rec, uint32_t* tiles_touched,
+                       const RecordArgs& rec, uint32_t* tiles_touched, unsigned long long* tile_desc,
                        cudaStream_t s) {
     if (sc.n == 0) return;
     const long long gpw = V < 32 ? 32 / V : 1;  // Gaussians per warp
     const long long warps = (sc.n + gpw - 1) / gpw;
     const unsigned nb = (unsigned)((warps + PRE_THREADS / 32 - 1) / (PRE_THREADS / 32));
 #define MVGS_PP(D) \
-    preprocess_kernel<D><<<nb, PRE_THREADS, 0, s>>>(sc, cams, V, tw, th, vis, rec, tiles_touched)
+    preprocess_kernel<D><<<nb, PRE_THREADS, 0, s>>>(sc, cams, V, tw, th, vis, rec, tiles_touched, tile_desc)
     switch (sc.sh_degree) {
         case 0: MVGS_PP(0); break;
         case 1: MVGS_PP(1); break;

@@ -377,8 +377,7 @@ struct DupSrc {
     const uint32_t* order;             // records by depth
     const unsigned long long* off;     // [R + 1] exclusive scan of tiles in that order
     Count R;
-    const short4* rect;
-    const int* rec_v;
+    const unsigned long long* desc;    // tile descriptors (pack_tile_desc), record order
     const DevCam* cams;
     uint32_t tiles;
 };
@@ -432,11 +431,10 @@ __global__ void __launch_bounds__(RS_THREADS, 4) dup_hist_kernel(DupSrc src, con
                                                              uint32_t* __restrict__ vals,
                                                              uint32_t* __restrict__ counts, uint32_t nblocks) {
     __shared__ uint32_t hist[RS_WARPS * 256];
-    // the block's record offsets and records (gathered once by all threads
-    // together: their loads are independent, so they are all in flight at
-    // once, instead of one dependent chain order -> rect, view -> camera per
-    // thread and record); after the generation the same bytes stage the
-    // block's entries for coalesced stores
+    // the block's record offsets and records (ids and tile descriptors,
+    // gathered once by all threads together: the loads are independent, so
+    // they are all in flight at once); after the generation the same bytes
+    // stage the block's entries for coalesced stores
     constexpr int OFF_BYTES = (RS_TILE + 4) * 4;
     constexpr int RAW_BYTES = OFF_BYTES + DUP_MAXR * 20;
     static_assert(RAW_BYTES >= RS_TILE * 8, "entry staging");
@@ -465,9 +463,10 @@ __global__ void __launch_bounds__(RS_THREADS, 4) dup_hist_kernel(DupSrc src, con
     if (staged) {
         for (int i = threadIdx.x; i < nr; i += RS_THREADS) {
             const uint32_t rec = src.order[rlo + i];
-            const DevCam& c = src.cams[src.rec_v[rec]];
+            const unsigned long long d = src.desc[rec];
+            const DevCam& c = src.cams[tile_desc_view(d)];
             s_rec[i] = rec;
-            s_rect[i] = src.rect[rec];
+            s_rect[i] = tile_desc_rect(d);
             s_base[i] = (uint32_t)c.tile_base;
             s_tx[i] = c.tiles_x;
         }
@@ -484,8 +483,9 @@ __global__ void __launch_bounds__(RS_THREADS, 4) dup_hist_kernel(DupSrc src, con
             rend = k0 + (uint64_t)(long long)s_off[li + 1];
         } else {
             rec = src.order[rr];
-            rc = src.rect[rec];
-            const DevCam& c = src.cams[src.rec_v[rec]];
+            const unsigned long long d = src.desc[rec];
+            rc = tile_desc_rect(d);
+            const DevCam& c = src.cams[tile_desc_view(d)];
             base = c.tile_base;
             txs = c.tiles_x;
             rend = src.off[rr + 1];
@@ -840,13 +840,13 @@ void radix_sort_pairs(const uint32_t* keys0, const uint32_t* vals0, uint32_t* ke
     }
 }
 
-void tile_sort(const uint32_t* order, const unsigned long long* tile_off, Count R, Count K, const short4* rect,
-               const int* rec_v, const DevCam* cams, long long tiles, int bits, uint32_t* keys_a, uint32_t* vals_a,
-               uint32_t* keys_b, uint32_t* vals_b, uint32_t* vals_out, void* tmp, cudaStream_t s) {
+void tile_sort(const uint32_t* order, const unsigned long long* tile_off, Count R, Count K,
+               const unsigned long long* desc, const DevCam* cams, long long tiles, int bits, uint32_t* keys_a,
+               uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b, uint32_t* vals_out, void* tmp, cudaStream_t s) {
     if (K.max == 0 || R.max == 0) return;
     // the radix pass uses the front of tmp; the block starts go behind it
     uint32_t* first_rec = reinterpret_cast<uint32_t*>(static_cast<char*>(tmp) + radix_temp_bytes(K.max));
-    const DupSrc src{order, tile_off, R, rect, rec_v, cams, (uint32_t)tiles};
+    const DupSrc src{order, tile_off, R, desc, cams, (uint32_t)tiles};
     const int passes = bits > 8 ? (bits + 7) / 8 : 1;
     // record ids take vb bits; two passes whose second digit fits beside them
     // in one word run packed (PassMode)
