@@ -144,8 +144,9 @@ mvgs_status check_config(const mvgs_config* cfg) {
         return fail(MVGS_EINVAL, "smem_batch must be 0, 64, 128 or 192");
     const int ppt = cfg->pixels_per_thread;
     if (ppt != 0) {
-        // a warp covers tile_w columns and (32 / tile_w) * ppt rows of a tile
-        if (!(ppt == 1 || ppt == 2 || ppt == 4 || ppt == 8) || th % ((32 / tw) * ppt))
+        // a warp covers a strip of blend_strip_width(tile_w) columns and
+        // (32 / that width) * ppt rows of a tile
+        if (!(ppt == 1 || ppt == 2 || ppt == 4 || ppt == 8) || th % ((32 / blend_strip_width(tw)) * ppt))
             return fail(MVGS_EINVAL, "pixels_per_thread %d does not fit a %dx%d tile", ppt, tw, th);
     }
     return MVGS_OK;
@@ -574,8 +575,9 @@ static mvgs_status render_impl(const mvgs_scene* scene, const mvgs_camera* cams,
     ba.th = th;
     ba.ppt = blend_pixels_per_thread(tw, th, cfg->pixels_per_thread);
     ba.wbatch = cfg->smem_batch ? cfg->smem_batch : 128;
-    ba.strip_h = (32 / tw) * ba.ppt;
-    ba.strips = th / ba.strip_h;
+    ba.sw = blend_strip_width(tw);
+    ba.strip_h = (32 / ba.sw) * ba.ppt;
+    ba.strips = (tw / ba.sw) * (th / ba.strip_h);
     ba.tiles = P.tiles;
     ba.ranges = ranges;
     ba.order = at<uint32_t>(state, L.off_tile_order);
@@ -636,8 +638,9 @@ static mvgs_status backward_impl(const mvgs_scene* scene, const mvgs_camera* cam
     ba.th = cfg->tile_h;
     ba.ppt = blend_pixels_per_thread(ba.tw, ba.th, cfg->pixels_per_thread);
     ba.wbatch = cfg->smem_batch ? cfg->smem_batch : 128;
-    ba.strip_h = (32 / ba.tw) * ba.ppt;
-    ba.strips = ba.th / ba.strip_h;
+    ba.sw = blend_strip_width(ba.tw);
+    ba.strip_h = (32 / ba.sw) * ba.ppt;
+    ba.strips = (ba.tw / ba.sw) * (ba.th / ba.strip_h);
     ba.tiles = P.tiles;
     ba.ranges = at<long long>(state, L.off_tile_ranges);
     ba.order = at<uint32_t>(state, L.off_tile_order);

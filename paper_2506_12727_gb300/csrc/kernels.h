@@ -131,8 +131,9 @@ struct BlendArgs {
     int tw, th;
     int ppt;                 // pixels per lane (resolved, 1..8)
     int wbatch;              // Gaussians per warp batch in shared memory (64, 128 or 192; 128 unless ppt 4)
-    int strip_h;             // rows of a warp's strip: (32 / tw) * ppt
-    int strips;              // strips per tile: th / strip_h
+    int sw;                  // columns of a warp's strip (blend_strip_width)
+    int strip_h;             // rows of a warp's strip: (32 / sw) * ppt
+    int strips;              // strips per tile: (tw / sw) * (th / strip_h)
     long long tiles;
     const long long* ranges;
     const uint32_t* order;   // tiles in processing order (longest lists first)
@@ -154,6 +155,9 @@ struct BlendArgs {
     const float* rec_depth;      // [records] camera depth
     float* depth_out;            // [pixels] or null
 };
+// Columns of a blend strip for a tile width (8: strips tile a 16- or 32-wide
+// tile two or four across).
+int blend_strip_width(int tw);
 // Pixels per lane for a tile size (req > 0: the caller's choice, checked).
 int blend_pixels_per_thread(int tw, int th, int req);
 // Persistent launches; `counter` is one device int of scratch (reset here).

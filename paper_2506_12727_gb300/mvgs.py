@@ -507,12 +507,14 @@ class Rasterizer:
         return partial_samples(self.cams_c, self.cfg, group, seed, self.device, stream, cell)
 
     def strip_cell(self):
-        """(tile_w, rows of a warp's strip) for this tile size and pixels per lane."""
+        """(columns, rows) of a warp's strip for this tile size and pixels per
+        lane (strips are 8 columns wide)."""
         tw, th = self.cfg.tile_w, self.cfg.tile_h
+        sw = min(tw, 8)
         ppt = self.cfg.pixels_per_thread
         if ppt == 0:
-            ppt = next(p for p in (4, 2, 1) if th % ((32 // tw) * p) == 0)
-        return (tw, (32 // tw) * ppt)
+            ppt = next(p for p in (4, 2, 1) if th % ((32 // sw) * p) == 0)
+        return (sw, (32 // sw) * ppt)
 
     def forward(self, scene_c, images=None, stream=None, samples: SampleSet | None = None, masked=False,
                 depth=False, stats=False):
