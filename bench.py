@@ -751,18 +751,17 @@ def stage_work(rz, needed, V, pixels, blended):
     }, blended
 
 
-# DRAM bytes (read + write) per blended pair of the blend kernels, from one
-# ncu capture of the kernels in the headline step, scaled by each launch's
-# blended pairs.  Valid only for the kernel source it was taken on: the
-# capture records a hash of the blend sources, and the line reports no
-# traffic once they differ.
+# DRAM bytes (read + write) per launch of the blend kernels, from the ncu
+# launch list of one headline step (dram__bytes_read.sum +
+# dram__bytes_write.sum).  Valid only for that workload and launch
+# configuration and for the blend sources it was taken on (their hash is
+# kept with it); otherwise the line reports no traffic.
 BLEND_TRAFFIC = {
-    # 500k SH-3 Gaussians, 4 views of 1264x832, 16x64 tiles: 449,569,394 blended pairs;
-    # forward 74.9 + 46.6 MB, backward 197.5 + 16.9 MB read + written per launch
-    "blend_forward": 121.5e6 / 449569394,
-    "blend_backward": 214.4e6 / 449569394,
-    "capture": "profiles/blend_kernels_multiview_500k_4x1264x832_16x64.md",
-    "sources_sha256": "e48d37a7fa37b41c30a9ed130543e1ecf93fb12c9b31e0c788cc4540d4486842",
+    "workload": "uneven_3m_8views", "tile": "32x64", "smem_batch": 64, "blended": 2118024889,
+    "blend_forward": 3743.7e6 + 171.0e6,
+    "blend_backward": 7645.4e6 + 591.9e6,
+    "capture": "profiles/launches_uneven_3m_8views.md",
+    "sources_sha256": "b76a92cf5395039bdb6ce4c2e43c2c0f711d885cbf2e17d0c533e3212e5dc66a",
 }
 
 
@@ -806,12 +805,17 @@ def roofline(stages, args, needed, rz, clk, V, pixels, blended):
     d["kernel"] = dom
     d["traffic"] = None
     if dom in ("blend_forward", "blend_backward") and blended:
-        if BLEND_TRAFFIC[dom] is not None and BLEND_TRAFFIC["sources_sha256"] == blend_sources_hash():
-            d["traffic"] = int(BLEND_TRAFFIC[dom] * blended)
-            d["traffic_source"] = (f"ncu dram__bytes (read + write) per blended pair of the kernel in "
-                                   f"{BLEND_TRAFFIC['capture']}, scaled by this launch's blended pairs")
-        else:
+        same_launch = (args.workload == BLEND_TRAFFIC["workload"] and
+                       f"{rz.cfg.tile_w}x{rz.cfg.tile_h}" == BLEND_TRAFFIC["tile"] and
+                       rz.cfg.smem_batch == BLEND_TRAFFIC["smem_batch"] and blended == BLEND_TRAFFIC["blended"])
+        if not same_launch:
+            d["traffic_source"] = "null: no ncu capture of this workload and launch configuration"
+        elif BLEND_TRAFFIC["sources_sha256"] != blend_sources_hash():
             d["traffic_source"] = "null: no ncu capture of the current blend sources"
+        else:
+            d["traffic"] = int(BLEND_TRAFFIC[dom])
+            d["traffic_source"] = (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel's launch "
+                                   f"in {BLEND_TRAFFIC['capture']} (same workload, tile, batch and sources)")
     if d["bound"] == "alu":
         per = FWD_FLOP_PER_BLENDED if dom == "blend_forward" else BWD_FLOP_PER_BLENDED
         d["algorithmic"] = f"{per} FLOP x {blended} blended (pixel, Gaussian) pairs per launch"

@@ -325,9 +325,11 @@ constexpr int PRE_THREADS = 128;
 // of the Gaussian-major list and every record field is stored coalesced (one
 // thread per Gaussian stored its records about V records apart from the next
 // thread's: partly written sectors).  The lanes of a Gaussian read the same
-// parameters (broadcast loads).
+// parameters (broadcast loads).  Compiled for 8 resident blocks per SM (64
+// registers): the kernel waits mostly on its loads, and the extra warps hide
+// more of them.
 template <int DEG>
-__global__ void __launch_bounds__(PRE_THREADS) preprocess_kernel(SceneArgs sc, const DevCam* __restrict__ cams, int V,
+__global__ void __launch_bounds__(PRE_THREADS, 8) preprocess_kernel(SceneArgs sc, const DevCam* __restrict__ cams, int V,
                                                                  int tw, int th, const uint8_t* __restrict__ vis,
                                                                  RecordArgs rec, uint32_t* __restrict__ tiles_touched,
                                                                  unsigned long long* __restrict__ tile_desc) {
@@ -341,10 +343,18 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_kernel(SceneArgs sc, c
     const int gi = lane / VG, vl = lane - gi * VG;
     const long long g = g0 + gi;
     const bool mine = gi < GPW && g < sc.n;
+    // the warp's Gaussians' SH rows (consecutive in memory) copied once into
+    // shared memory by all lanes, with loads issued before any arithmetic
+    constexpr int E = NK * 3;
+    __shared__ float s_sh[PRE_THREADS / 32][32 * E];
+    float* wsh = s_sh[threadIdx.x >> 5];
+    const int gcount = (int)(sc.n - g0 < GPW ? sc.n - g0 : GPW);
+    const float* rows = sc.sh + (size_t)g0 * E;
+    for (int i = lane; i < gcount * E; i += 32) wsh[i] = __ldg(rows + i);
     Gauss G;
     if (mine) load_gauss(sc, g, G, true);
-    const float* shg = sc.sh + (size_t)(mine ? g : g0) * NK * 3;
-    const bool sh_vec = (reinterpret_cast<uintptr_t>(sc.sh) & 15) == 0;  // rows of 48 floats stay 16-byte aligned
+    __syncwarp();
+    const float* shc = wsh + (mine ? gi : 0) * E;
     long long rbase = rec.rec_off[g0];
     for (int c = 0; c < V; c += VG) {
         const int v = c + vl;
@@ -371,7 +381,8 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_kernel(SceneArgs sc, c
         sh_basis<DEG>(dx, dy, dz, Y);
         float rgb[3] = {0.5f, 0.5f, 0.5f};
         int clamp = 0;
-        for_each_sh<NK>(shg, sh_vec, [&](int e, float coef) { rgb[e % 3] += Y[e / 3] * coef; });
+#pragma unroll
+        for (int e = 0; e < E; e++) rgb[e % 3] += Y[e / 3] * shc[e];
 #pragma unroll
         for (int ch = 0; ch < 3; ch++) {
             if (rgb[ch] < 0.f) { clamp |= 1 << ch; rgb[ch] = 0.f; }
