@@ -472,36 +472,39 @@ __global__ void __launch_bounds__(RS_THREADS, 4) dup_hist_kernel(DupSrc src, con
         }
     }
     __syncthreads();
-    // record rr: id, rectangle, view tile base, tiles per row, end of its entries
-    auto load = [&](uint64_t rr, uint32_t& rec, short4& rc, long long& base, int& txs, uint64_t& rend) {
+    // record rr: id, rectangle, view tile base, tiles per row, end of its
+    // entries relative to the block's first entry (32-bit arithmetic in the
+    // walk: tile ids and entry positions are below 2^32)
+    auto load = [&](uint64_t rr, uint32_t& rec, short4& rc, uint32_t& base, int& txs, uint32_t& rend) {
         if (staged) {
             const int li = (int)(rr - rlo);
             rec = s_rec[li];
             rc = s_rect[li];
             base = s_base[li];
             txs = s_tx[li];
-            rend = k0 + (uint64_t)(long long)s_off[li + 1];
+            rend = (uint32_t)s_off[li + 1];
         } else {
             rec = src.order[rr];
             const unsigned long long d = src.desc[rec];
             rc = tile_desc_rect(d);
             const DevCam& c = src.cams[tile_desc_view(d)];
-            base = c.tile_base;
+            base = (uint32_t)c.tile_base;
             txs = c.tiles_x;
-            rend = src.off[rr + 1];
+            rend = (uint32_t)(src.off[rr + 1] - k0);
         }
     };
     uint32_t* wh = hist + (threadIdx.x >> 5) * 256;
-    const uint64_t first = k0 + (uint64_t)threadIdx.x * DUP_ITEMS;
+    const uint32_t cnt_l = (uint32_t)(K - k0 < (uint64_t)RS_TILE ? K - k0 : (uint64_t)RS_TILE);
+    const uint32_t first_l = (uint32_t)threadIdx.x * DUP_ITEMS;
+    const uint32_t tmax = src.tiles - 1u;
     uint32_t kk[DUP_ITEMS], vv[DUP_ITEMS];
 #pragma unroll
     for (int i = 0; i < DUP_ITEMS; i++) kk[i] = vv[i] = 0u;
-    if (first < K) {
+    if (first_l < cnt_l) {
+        const uint64_t first = k0 + first_l;
         uint64_t r = dup_record(src, s_off, rlo, nr, k0, first);
-        uint64_t rend;
-        uint32_t rec;
+        uint32_t rend, rec, base;
         short4 rc;
-        long long base;
         int txs;
         load(r, rec, rc, base, txs, rend);
         int w = max(rc.z - rc.x, 1);
@@ -510,17 +513,17 @@ __global__ void __launch_bounds__(RS_THREADS, 4) dup_hist_kernel(DupSrc src, con
         int tx = rc.x + (int)(j % (uint32_t)w), ty = rc.y + (int)(j / (uint32_t)w);
 #pragma unroll
         for (int i = 0; i < DUP_ITEMS; i++) {
-            const uint64_t idx = first + i;
-            if (idx < K) {
-                while (idx >= rend) {  // next record (skipping any without tiles)
+            const uint32_t l = first_l + i;
+            if (l < cnt_l) {
+                while (l >= rend) {  // next record (skipping any without tiles)
                     r++;
                     load(r, rec, rc, base, txs, rend);
                     w = max(rc.z - rc.x, 1);
                     tx = rc.x;
                     ty = rc.y;
                 }
-                const long long t = base + (long long)ty * txs + tx;
-                const uint32_t key = (uint32_t)(t < (long long)src.tiles ? t : (long long)src.tiles - 1);
+                const uint32_t t = base + (uint32_t)ty * (uint32_t)txs + (uint32_t)tx;
+                const uint32_t key = t < tmax ? t : tmax;
                 kk[i] = key;
                 vv[i] = rec;
                 atomicAdd(&wh[key & 0xffu], 1u);
