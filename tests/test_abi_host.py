@@ -93,6 +93,14 @@ def test_bad_arguments_are_rejected(lib):
         lib.render_layout(10, bad, cfg, lib.Capacity(10, 10))
     assert e.value.status == lib.EINVAL
     assert "empty image" in lib.last_error()
+    # tile coordinates travel in 12-bit fields: at most 4095 tiles along an axis of a view
+    wide = lib.make_cameras(synth.make_cameras([(8 * 4095, 64)]))
+    lib.render_layout(10, wide, lib.make_config((8, 8)), lib.Capacity(10, 10))
+    wider = lib.make_cameras(synth.make_cameras([(8 * 4095 + 1, 64)]))
+    with pytest.raises(lib.MvgsError) as e:
+        lib.render_layout(10, wider, lib.make_config((8, 8)), lib.Capacity(10, 10))
+    assert e.value.status == lib.EOVERFLOW
+    assert "4095 tiles per axis" in lib.last_error()
     cfg.flags = 16  # only bits 1, 2, 4 and 8 (masked partial, depth, capturable, pixel stats) are defined
     with pytest.raises(lib.MvgsError):
         lib.render_layout(10, cc, cfg, lib.Capacity(10, 10))
