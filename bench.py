@@ -758,10 +758,10 @@ def stage_work(rz, needed, V, pixels, blended):
 # kept with it); otherwise the line reports no traffic.
 BLEND_TRAFFIC = {
     "workload": "uneven_3m_8views", "tile": "32x64", "smem_batch": 64, "blended": 2118024889,
-    "blend_forward": 3743.7e6 + 171.0e6,
-    "blend_backward": 7645.4e6 + 591.9e6,
+    "blend_forward": 3567.5e6 + 170.9e6,
+    "blend_backward": 7717.4e6 + 597.1e6,
     "capture": "profiles/launches_uneven_3m_8views.md",
-    "sources_sha256": "b76a92cf5395039bdb6ce4c2e43c2c0f711d885cbf2e17d0c533e3212e5dc66a",
+    "sources_sha256": "dd1c78333a597ebf4b435a5071c45a58e13c28fe41e70736313e473d84e4dadd",
 }
 
 

@@ -412,6 +412,8 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(Bl
                 n += __popc(bal);
             }
             __syncwarp();
+            // two Gaussians per loop trip: one's reduce-scatter overlaps the next one's pixels
+#pragma unroll 2
             for (int j = 0; j < n; j++) {
                 const uint32_t pos = wpos[j];
                 float g[10];
