@@ -761,16 +761,22 @@ BLEND_TRAFFIC = {
     "blend_forward": 3567.5e6 + 170.9e6,
     "blend_backward": 7717.4e6 + 597.1e6,
     "capture": "profiles/launches_uneven_3m_8views.md",
-    "sources_sha256": "dd1c78333a597ebf4b435a5071c45a58e13c28fe41e70736313e473d84e4dadd",
+    "sources_sha256": "3dd3d55a1c09a25f51883caca8d5d4aa3d57893a95ff10ec5c975f95727c9edb",
 }
 
 
 def blend_sources_hash():
+    """SHA-256 of the blend sources' code: comments and blank lines left out,
+    so that a comment edit does not invalidate a capture."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("blend.cu", "common.cuh"):
-        with open(os.path.join(ROOT, "paper_2506_12727_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2506_12727_gb300", "csrc", f)) as fh:
+            for line in fh:
+                code = re.sub(r"//.*$", "", line).rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()
 
 

@@ -103,9 +103,10 @@ typedef struct mvgs_config {
     float bg[3];      /* background colour added with the final transmittance */
     uint32_t flags;   /* MVGS_FLAG_* bits below (0 = none) */
     int32_t pixels_per_thread;  /* blend lanes each own this many pixels of a
-                                   tile column, so one warp blends a strip of
-                                   tile_w columns by (32 / tile_w) *
-                                   pixels_per_thread rows: 0 = automatic, else
+                                   pixel column, so one warp blends a strip of
+                                   w = min(tile_w, 8) columns by (32 / w) *
+                                   pixels_per_thread rows (strips side by side
+                                   across wider tiles): 0 = automatic, else
                                    1, 2, 4 or 8 with the strip height dividing
                                    tile_h.  Results do not depend on it. */
     int32_t smem_batch;         /* Gaussians a warp stages in shared memory per

@@ -3,8 +3,9 @@
 // In the supplement's rasterizer every (tile, view) pair gets its own thread
 // block, and Alg. 2 has a tile's threads fetch its depth-sorted Gaussians
 // into shared memory batch by batch and blend them.  Here the unit of work is a strip of
-// a (tile, view) pair -- tile_w columns by (32 / tile_w) * PPT rows -- owned by
-// one warp: each lane owns PPT pixels of one column, the warp stages batches
+// a (tile, view) pair -- 8 columns (blend_strip_width) by (32 / 8) * PPT rows,
+// strips side by side across wider tiles -- owned by one warp: each lane owns
+// PPT pixels of one column, the warp stages batches
 // of the tile's list in its own slice of shared memory, and leaves the strip
 // as soon as all its pixels have stopped.  Warps of a persistent launch take
 // strips from a queue that lists the tiles with the longest lists first, so
