@@ -142,3 +142,20 @@ def test_window_loss_gradients_match_oracle(full, cuda_lib):
     gm = np.zeros((scene.n * cams.V, 2))
     gm[D["valid"] != 0] = gm2d.cpu().numpy()[D["rec_index"][D["valid"] != 0]]
     assert_close_frac(gm[vis], g2d[vis, :2], 1e-3, 1e-6 * np.abs(g2d[:, :2]).max(), "mean2d")
+
+
+def test_image_does_not_depend_on_the_tile_size(full, cuda_lib):
+    """The full-size image at 16x16 tiles equals the one at the benchmark's tile
+    bit for bit.  At 3M x 8 views this also runs the tile sort's unpacked
+    two-pass path: 16-bit tile ids (44,400 tiles) with 24M records do not fit
+    one packed word."""
+    if full["tile"] == (16, 16):
+        pytest.skip("already at 16x16 tiles")
+    rz = cuda_lib.Rasterizer(full["cams"], tile=(16, 16))
+    img = rz.forward(full["sc"])
+    torch.cuda.synchronize()
+    assert torch.equal(img.cpu(), torch.tensor(full["img"], dtype=torch.float32))
+    if full["name"] == "uneven_3m_8views":
+        assert int(rz.layout.tiles) > 32768 and int(rz.needed.records) > (1 << 24)
+    del rz, img
+    torch.cuda.empty_cache()
