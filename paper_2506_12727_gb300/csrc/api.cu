@@ -708,7 +708,8 @@ static size_t count_ws_parts(long long n, size_t* a, size_t* b, size_t* c) {
     const long long nn = n > 0 ? n : 1;
     *a = ((size_t)nn * sizeof(int) + 255) / 256 * 256;
     *b = ((size_t)(nn + 1) * sizeof(long long) + 255) / 256 * 256;
-    *c = scan_temp_bytes((uint64_t)nn);
+    // rounded up: the camera table (16-byte aligned structs) follows it
+    *c = (scan_temp_bytes((uint64_t)nn) + 255) / 256 * 256;
     return 256 + 2 * *a + 2 * *b + *c;
 }
 

@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) blend_backward_kernel(Bl
                     if (my_val >= 2 && my_val <= 4)
                         atomicAdd(rec_conic + (size_t)3 * wrid[j] + (my_val - 2), (double)sum);
                     else
-                        atomicAdd(rec_grad + (size_t)kGradStride * wrid[j] + my_val, sum);
+                        atomicAdd(rec_grad + (size_t)kGradStride * wrid[j] + grad_slot(my_val), sum);
                 }
             }
         }

@@ -54,10 +54,13 @@ struct CamChunk {
     DevCam c[kCamChunk];
 };
 
-// Per-record gradient slots written by the blend backward and read by the
-// preprocessing backward: mean2d (2), conic A B C (3), opacity (1), rgb (3),
-// E_1 term (1), padding (2).
-constexpr int kGradStride = 12;
+// Per-record float gradient slots written by the blend backward and read by
+// the preprocessing backward: mean2d x, y, opacity, r, g, b, E_1 term,
+// padding (the conic's three go to a separate double array).  The blend
+// backward's reduced value v (0, 1 mean2d; 2..4 conic; 5 opacity; 6..8 rgb;
+// 9 E_1) goes to float slot grad_slot(v).
+constexpr int kGradStride = 8;
+__host__ __device__ constexpr int grad_slot(int v) { return v < 2 ? v : v - 3; }
 
 // Global tile ids index the view-major list of (view, tile) pairs.
 // Single-instruction approximations (PTX rcp.approx / sqrt.approx, about

@@ -69,8 +69,8 @@ void launch_preprocess(const SceneArgs& sc, const DevCam* cams, int V, int tw, i
                        const RecordArgs& rec, uint32_t* tiles_touched, unsigned long long* tile_desc,
                        cudaStream_t s);
 void launch_zero_f32(float* p, size_t count, cudaStream_t s);
-// rec_grad: [records, kGradStride] float (mean2d, -, -, -, opacity, rgb, e1 at
-// 0, 1, 5, 6..8, 9); rec_conic: [records, 3] double (conic A, B, C).
+// rec_grad: [records, kGradStride] float (mean2d x, y, opacity, rgb, e1 at
+// 0, 1, 2, 3..5, 6); rec_conic: [records, 3] double (conic A, B, C).
 void launch_preprocess_backward(const SceneArgs& sc, const DevCam* cams, int V, const RecordArgs& rec,
                                 const float* rec_grad, const double* rec_conic, float* g_means,
                                 float* g_log_scales, float* g_quats, float* g_logits, float* g_sh,

@@ -396,9 +396,12 @@ __global__ void __launch_bounds__(PRE_THREADS, 8) preprocess_kernel(SceneArgs sc
     }
 }
 
-__global__ void zero_kernel(float4* __restrict__ p, size_t n4) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
-        p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+// Zeroes count floats: float4 stores, then the last count % 4 one by one.
+__global__ void zero_kernel(float4* __restrict__ p, size_t count) {
+    const size_t n4 = count / 4;
+    const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (size_t i = i0; i < n4; i += (size_t)gridDim.x * blockDim.x) p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i0 < count % 4) reinterpret_cast<float*>(p)[4 * n4 + i0] = 0.f;
 }
 
 // Chain rule from the per-record 2D gradients to the Gaussian parameters;
@@ -436,17 +439,16 @@ __global__ void __launch_bounds__(128, 3) preprocess_backward_kernel(SceneArgs s
         const DevCam& cam = cams[rec.rec_v[r]];
         Proj P;
         project(G, cam, 1, 1, P);  // same arithmetic as the forward; the tile size only affects the rect
-        const float4 q0 = *reinterpret_cast<const float4*>(rg + kGradStride * r);
-        const float4 q1 = *reinterpret_cast<const float4*>(rg + kGradStride * r + 4);
-        const float4 q2 = *reinterpret_cast<const float4*>(rg + kGradStride * r + 8);
-        const float gx = q0.x, gy = q0.y, gop = q1.y;
+        const float4 q0 = *reinterpret_cast<const float4*>(rg + kGradStride * r);      // x, y, opacity, r
+        const float4 q1 = *reinterpret_cast<const float4*>(rg + kGradStride * r + 4);  // g, b, E_1, -
+        const float gx = q0.x, gy = q0.y, gop = q0.z;
         const float gA = (float)rc[3 * r], gB = (float)rc[3 * r + 1], gC = (float)rc[3 * r + 2];
-        const float grgb_raw[3] = {q1.z, q1.w, q2.x};
+        const float grgb_raw[3] = {q0.w, q1.x, q1.y};
         if (out_mean2d) {
             out_mean2d[2 * r] = gx;
             out_mean2d[2 * r + 1] = gy;
         }
-        if (out_e1) out_e1[r] = q2.y;
+        if (out_e1) out_e1[r] = q1.z;
         // conic Q = Sigma'^-1 = [[A, B], [B, C]] = [[c, -b], [-b, a]] / det; with
         // dQ = -Q dSigma' Q, dL/dSigma' = -Q G Q for G = [[gA, gB/2], [gB/2, gC]]
         // (gB is the derivative w.r.t. B filling both off-diagonal entries, and
@@ -648,11 +650,12 @@ void launch_preprocess(const SceneArgs& sc, const DevCam* cams, int V, int tw, i
 
 void launch_zero_f32(float* p, size_t count, cudaStream_t s) {
     if (count == 0) return;
-    // counts handed in are multiples of 4 floats (record slots of 12 floats)
+    // p is 16-byte aligned; any count
     const size_t n4 = count / 4;
     unsigned nb = (unsigned)((n4 + 255) / 256);
+    if (nb == 0) nb = 1;
     if (nb > 65535u * 8u) nb = 65535u * 8u;
-    zero_kernel<<<nb, 256, 0, s>>>(reinterpret_cast<float4*>(p), n4);
+    zero_kernel<<<nb, 256, 0, s>>>(reinterpret_cast<float4*>(p), count);
     note_launches(1);
 }
 

@@ -360,3 +360,43 @@ def test_optional_outputs_do_not_change_the_render(cuda_lib):
     st = runs[2][3].to(torch.int64)
     assert bool((st[:, 1] <= runs[2][2].to(torch.int64)).all())
     assert bool((runs[2][2].to(torch.int64) <= st[:, 0]).all())
+
+
+def test_backward_with_an_exact_odd_record_capacity(cuda_lib):
+    """Capacities exactly the records and keys needed, with an odd record
+    count: the per-record gradient slots (8 floats and 3 doubles per record)
+    are zeroed to their last byte before the backward's atomics, whatever the
+    workspace held (filled with NaN bytes here).  The pre-count runs on 6000
+    Gaussians and fewer, where its scan scratch is not a multiple of 16 bytes
+    (the camera table behind it must still be aligned)."""
+    scene, cams = CASES["multiview_sh3_ragged"]
+    params = scene_to_device(scene)
+    cams_c = cuda_lib.make_cameras(cams)
+    cfg = cuda_lib.make_config((16, 16))
+    # the first Gaussian count (from all of them down) with an odd record count
+    for n in range(scene.n, scene.n - 32, -1):
+        keep = {k: v[:n].contiguous() for k, v in params.items()}
+        sck = cuda_lib.make_scene(keep, scene.sh_degree)
+        need = cuda_lib.count_views(sck, cams_c, cfg)
+        if int(need.records) % 2 == 1:
+            break
+    else:
+        pytest.skip("no odd record count")
+    cap = cuda_lib.Capacity(int(need.records), int(need.keys))
+    L = cuda_lib.render_layout(n, cams_c, cfg, cap)
+    state = torch.empty(L.state_bytes, dtype=torch.uint8, device="cuda")
+    ws = torch.full((L.workspace_bytes,), 0xFF, dtype=torch.uint8, device="cuda")
+    probe = cuda_lib.Rasterizer(cams, tile=(16, 16))
+    img = probe.forward(sck)
+    dimg = torch.randn(img.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    exp = grads_like(keep)
+    probe.backward(sck, dimg, exp)
+    img2 = torch.empty_like(img)
+    cuda_lib.render_views(sck, cams_c, cfg, cap, img2, state, ws)
+    got = grads_like(keep)
+    cuda_lib.render_views_backward(sck, cams_c, cfg, cap, dimg, state, ws, got)
+    torch.cuda.synchronize()
+    assert torch.equal(img2, img)
+    for k in got:
+        assert torch.isfinite(got[k]).all(), k
+        torch.testing.assert_close(got[k], exp[k], rtol=1e-4, atol=1e-6 * float(exp[k].abs().max()))
