@@ -758,10 +758,10 @@ def stage_work(rz, needed, V, pixels, blended):
 # kept with it); otherwise the line reports no traffic.
 BLEND_TRAFFIC = {
     "workload": "uneven_3m_8views", "tile": "32x64", "smem_batch": 64, "blended": 2118024889,
-    "blend_forward": 3567.5e6 + 170.9e6,
-    "blend_backward": 7717.4e6 + 597.1e6,
+    "blend_forward": 3720.0e6 + 170.8e6,
+    "blend_backward": 7450.7e6 + 419.6e6,
     "capture": "profiles/launches_uneven_3m_8views.md",
-    "sources_sha256": "3dd3d55a1c09a25f51883caca8d5d4aa3d57893a95ff10ec5c975f95727c9edb",
+    "sources_sha256": "a114b24ee0915ba63bfb74ce3df782c2859888aed9232cb2cd9b4c1a09a8e591",
 }
 
 
