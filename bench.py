@@ -734,18 +734,27 @@ def stage_work(rz, needed, V, pixels, blended):
     tiles = int(rz.layout.tiles)
     bits = max(1, int(np.ceil(np.log2(max(tiles, 2)))))
     passes = max(1, (bits + 7) // 8)
+    vb = max(1, int(R - 1).bit_length())  # record-id bits
+    if passes == 2 and (bits - 8) + vb <= 32:
+        # packed two-pass tile sort: duplication writes a 16-bit tile id and a
+        # record id, pass 0 reads them and writes one word, pass 1 reads it
+        # twice (histogram, scatter) and writes the record id; the duplication
+        # reads each record's id, descriptor and entry offset
+        tile_sort_bytes = 28.0 * K + 20.0 * R
+    else:
+        tile_sort_bytes = 8.0 * K + passes * 16.0 * K - 4.0 * K + 20.0 * R
     return {
         "count_visible": ("hbm", 44.0 * n + 4.0 * n + n * V, "B"),
         "scan_records": ("hbm", 12.0 * n, "B"),
         "preprocess": ("hbm", 236.0 * n + n * V + 8.0 * n + 76.0 * R, "B"),
         "depth_sort": ("hbm", 4 * 16.0 * R, "B"),
         "scan_tiles": ("hbm", 12.0 * R, "B"),
-        "tile_sort": ("hbm", 8.0 * K + passes * 16.0 * K - 4.0 * K, "B"),
+        "tile_sort": ("hbm", tile_sort_bytes, "B"),
         "ranges": ("hbm", 8.0 * R + 24.0 * tiles, "B"),
         "blend_forward": ("alu", FWD_FLOP_PER_BLENDED * blended, "FLOP"),
-        "zero_grads": ("hbm", 48.0 * R, "B"),
+        "zero_grads": ("hbm", 56.0 * R, "B"),  # 8 float and 3 double slots per record
         "blend_backward": ("alu", BWD_FLOP_PER_BLENDED * blended, "FLOP"),
-        "preprocess_backward": ("hbm", 472.0 * n + 124.0 * R, "B"),
+        "preprocess_backward": ("hbm", 472.0 * n + 76.0 * R, "B"),
         "dssim": ("hbm", 44.0 * 3 * pixels, "B"),
         "adc": ("hbm", 12.0 * R + 32.0 * n, "B"),
     }, blended

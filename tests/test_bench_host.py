@@ -44,5 +44,9 @@ def test_blend_work_counts_blended_pairs():
     assert blended == 123456
     assert work["blend_forward"] == ("alu", bench.FWD_FLOP_PER_BLENDED * 123456, "FLOP")
     assert work["blend_backward"] == ("alu", bench.BWD_FLOP_PER_BLENDED * 123456, "FLOP")
-    # 300 tiles: 9 bits, 2 passes: keys written once, 16 B per entry and pass, the last pass without keys
-    assert work["tile_sort"] == ("hbm", 8.0 * 40000 + 2 * 16.0 * 40000 - 4.0 * 40000, "B")
+    # 300 tiles: 9 bits, 2 passes, 2500 records (12-bit ids): packed, 28 B per entry and 20 B per record
+    assert work["tile_sort"] == ("hbm", 28.0 * 40000 + 20.0 * 2500, "B")
+    # 70,000 tiles (17 bits, 3 passes): unpacked, 8 B written by the duplication, 16 B per entry and pass
+    rz3 = types.SimpleNamespace(n=1000, layout=types.SimpleNamespace(tiles=70000))
+    work3, _ = bench.stage_work(rz3, (2500, 40000), 4, 10000, 1)
+    assert work3["tile_sort"] == ("hbm", 8.0 * 40000 + 3 * 16.0 * 40000 - 4.0 * 40000 + 20.0 * 2500, "B")
