@@ -108,8 +108,10 @@ void radix_sort_pairs(const uint32_t* keys0, const uint32_t* vals0, uint32_t* ke
 // tile) taken in the order of `order` (records sorted by depth); tile_off is
 // the exclusive scan of the records' tile counts in that order; desc holds the
 // records' tile descriptors (pack_tile_desc, record order).  The entries
-// are generated inside the first radix pass.  Sorted record ids end in
-// vals_out; keys_a/b and vals_a/b are scratch of K entries.
+// are generated by the first pass's histogram kernel (the duplication) and
+// written to keys_a / vals_a (16-bit tile ids when the sort runs packed).
+// Sorted record ids end in vals_out; keys_a/b and vals_a/b are scratch of K
+// entries.
 void tile_sort(const uint32_t* order, const unsigned long long* tile_off, Count R, Count K,
                const unsigned long long* desc, const DevCam* cams, long long tiles, int bits, uint32_t* keys_a,
                uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b, uint32_t* vals_out, void* tmp, cudaStream_t s);

@@ -178,7 +178,7 @@ struct RankSmem {
     uint32_t dstart[256];            // first block-local position of each digit
     uint32_t scan_buf[33];
     uint32_t skeys[RS_TILE];         // keys in block-local sorted order
-    uint32_t svals[RS_TILE + 1];     // values in block-local sorted order (+1: see dup_downsweep)
+    uint32_t svals[RS_TILE];         // values in block-local sorted order
 };
 
 // How a pass stores its output.  A two-pass sort of keys of at most 16 bits
